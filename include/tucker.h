@@ -1,0 +1,194 @@
+/*
+ * tucker.h -- C ABI of libtucker: the HOOI hot path for sparse Tucker
+ * decomposition (Chakaravarthy et al., "On Optimizing Distributed Tucker
+ * Decomposition for Sparse Tensors", arXiv:1804.09494) on one NVIDIA GB300.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - A tensor has N modes (2 <= N <= 6) of lengths L[0..N-1] and a core of
+ *    size K[0..N-1], 1 <= K[n] <= min(L[n], 32) (Section 2.2: K_n <= L_n).
+ *    Indices are 0-based (the paper is 1-based).
+ *  - Khat_n = prod_{m != n} K[m] is the row length of the penultimate matrix
+ *    Z_(n) (Section 2.2); it must be <= 4096.
+ *  - Precision: a context is FP32 ("mixed": FP32 TTM-chain, FP32 Gram with
+ *    FP64 reductions, FP64 eigen-polish, Cholesky and reductions) or FP64
+ *    (plain FP64 everywhere).  Every "real" buffer below is float for FP32
+ *    contexts and double for FP64 contexts, except where double is stated.
+ *  - Pointers prefixed d_ are device pointers, h_ are host pointers.  The
+ *    caller owns every buffer it passes; the library owns its workspace.
+ *  - Factor matrices F_m are L[m] x K[m], row-major, leading dimension K[m].
+ *  - Z_(n) is returned *compact*: only the R_n non-empty slices (Section 3,
+ *    "truncated local copy"), as an R_n x Khat_n row-major matrix whose row r
+ *    belongs to slice d_row_id[r]; rows are in increasing slice id.  Columns
+ *    follow Section 2.1 / Appendix A: the first remaining mode varies fastest.
+ *  - The core G is prod K entries, first mode fastest.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) unless it says it synchronises.
+ *  - Errors: a call returns TUCKER_OK or an error code; tucker_last_error()
+ *    gives the message.  Arguments are checked on the host before anything is
+ *    launched.  A device-side failure (e.g. a Cholesky breakdown) is latched
+ *    in the context and returned by the next call that synchronises.
+ */
+#ifndef TUCKER_H
+#define TUCKER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tucker_ctx* tucker_t;
+
+typedef enum {
+  TUCKER_OK = 0,
+  TUCKER_ERR_ARG = 1,      /* invalid argument (host-side validation)              */
+  TUCKER_ERR_OOM = 2,      /* device allocation failed                             */
+  TUCKER_ERR_CUDA = 3,     /* a CUDA runtime call failed                           */
+  TUCKER_ERR_NUMERIC = 4,  /* numeric breakdown (Cholesky pivot <= 0, non-finite)  */
+  TUCKER_ERR_TIMEOUT = 5,  /* reserved: a bounded device wait ran out              */
+  TUCKER_ERR_STATE = 6,    /* call not valid for this context                      */
+  TUCKER_ERR_INDEX = 7     /* an input coordinate lies outside [0, L[m])           */
+} tucker_status;
+
+typedef enum { TUCKER_FP32 = 0, TUCKER_FP64 = 1 } tucker_prec;
+
+typedef struct {
+  int32_t prec;          /* tucker_prec                                                  */
+  int32_t P_bins;        /* Lite bins per mode (one TTM-chain thread each); 0 = one per   *
+                          * resident thread, from the device's SM count and occupancy     */
+  int32_t gauss_seidel;  /* 0 = Fig. 1 as printed (every mode from the input factors),     *
+                          * 1 = textbook HOOI (each mode sees the factors refined so far) */
+  int32_t timing;        /* 1 = record CUDA events around every phase (tucker_timings)    */
+  int32_t reserved[8];   /* must be zero                                                  */
+} tucker_opts;
+
+/* Fills *opts with the defaults (FP32, automatic P, Jacobi reading, no timing). */
+void tucker_default_opts(tucker_opts* opts);
+
+/*
+ * tucker_init -- builds a context for one COO tensor (Section 3: the element
+ * set E with coordinates (l_1..l_N) and values val(e)).
+ *
+ * For every mode n it runs the Lite distribution (Section 6.1, Fig. 7) with P
+ * bins, one bin per TTM-chain thread: slice histogram, sort of the non-empty
+ * slices by (cardinality, slice id), stage 1 round robin under the limit
+ * ceil(nnz/P), stage 2 contiguous fill; and it stores a permuted copy of the
+ * tensor grouped bin by bin ("multi-policy scheme", Section 3), so the
+ * caller may free its COO arrays once this call returns.
+ *   N, L, K  : host arrays as above.
+ *   nnz      : number of elements, 1 <= nnz < 2^31; coordinates must be distinct.
+ *   d_idx    : host array of N device pointers; d_idx[m] holds nnz int32 coordinates.
+ *   d_val    : nnz values (float or double per opts->prec).
+ *   opts     : NULL = defaults.
+ * Synchronises `stream`.  Returns TUCKER_ERR_INDEX if a coordinate is out of
+ * range, TUCKER_ERR_ARG for bad sizes or non-finite values, TUCKER_ERR_OOM if
+ * the workspace does not fit.  On error *out is NULL.
+ */
+tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t* K, int64_t nnz,
+                          const int32_t* const* d_idx, const void* d_val, const tucker_opts* opts,
+                          void* stream);
+
+/* Releases the context and all library-owned device memory (synchronises). */
+void tucker_destroy(tucker_t t);
+
+/* Message of the last error on this context (or of the last failed init when t is NULL). */
+const char* tucker_last_error(tucker_t t);
+
+/*
+ * tucker_stats -- Section 4.1 metrics of the mode-n Lite partition and the
+ * compact row count.  E_max = max_p |E_n^p|, R_sum = sum_p R_n^p,
+ * R_max = max_p R_n^p, R_n = number of non-empty slices, P = bins.
+ * Any output pointer may be NULL.  Host-only, does not touch the device.
+ */
+tucker_status tucker_stats(tucker_t t, int mode, int64_t* E_max, int64_t* R_sum, int64_t* R_max,
+                           int64_t* R_n, int64_t* P);
+
+/*
+ * tucker_partition -- exports the mode-n partition for checking: bin p owns
+ * the original element ids d_perm[d_bin_ptr[p] .. d_bin_ptr[p+1]), in the
+ * order the Lite pseudocode assigns them (stage-1 slices in sorted order,
+ * then stage-2 pieces; original COO order inside a slice).
+ *   d_bin_ptr : P+1 int64 (device), d_perm : nnz int32 (device).
+ */
+tucker_status tucker_partition(tucker_t t, int mode, int64_t* d_bin_ptr, int32_t* d_perm, void* stream);
+
+/*
+ * ttm_chain -- penultimate matrix Z_(n) = T x_{m != n} F_m^T (Fig. 1
+ * "TTM-Chain") through the Kronecker reformulation of Section 3, eq. (1):
+ * Z_(n)[l,:] = sum_{e in Slice_n^l} val(e) Kron_n(e), Kron_n as in Appendix A.
+ *   d_F      : host array of N device pointers to the factors (entry `mode` unused, may be NULL).
+ *   d_vals   : NULL = the tensor's own values; else nnz replacement values in
+ *              original element order (used for differentiation w.r.t. values).
+ *   d_Z      : output, R_n x Khat_n (compact, see above).
+ *   d_row_id : output, R_n int32 slice ids (may be NULL).
+ * Owned slices are summed by one thread each; slices Lite splits over bins
+ * are summed by a fixed-order fix-up, so the result is deterministic.
+ */
+tucker_status ttm_chain(tucker_t t, int mode, const void* const* d_F, const void* d_vals, void* d_Z,
+                        int32_t* d_row_id, void* stream);
+
+/*
+ * factor_update -- new factor F~_n = leading K_n left singular vectors of
+ * Z_(n) (Fig. 1 "SVD"), computed as: Gram W = Z^T Z (FP64 result), top-K_n
+ * eigenpairs of W, back-projection U = Z V Sigma^-1, CholeskyQR2 of U, column
+ * signs fixed so that each column's entry of largest magnitude (lowest slice
+ * id on a tie) is positive, rows of empty slices zero.
+ *   d_Z     : R_n x Khat_n compact matrix as produced by ttm_chain for this mode.
+ *   d_F_out : output, L[mode] x K[mode].
+ *   d_sigma : output, K[mode] doubles (singular values, descending); may be NULL.
+ * Latches TUCKER_ERR_NUMERIC if U is rank deficient (e.g. R_n < K_n).
+ */
+tucker_status factor_update(tucker_t t, int mode, const void* d_Z, void* d_F_out, double* d_sigma,
+                            void* stream);
+
+/*
+ * core -- G = T x_1 F_1^T x_2 ... x_N F_N^T (Fig. 1 "New core"), computed as
+ * F_n*^T Z_(n*) for the cheapest mode n*.  d_G: prod K values, first mode fastest.
+ */
+tucker_status core(tucker_t t, const void* const* d_F, void* d_G, void* stream);
+
+/*
+ * hooi_iter -- one invocation of the HOOI procedure (Fig. 1): for every mode
+ * n, ttm_chain + factor_update, then the new core and the fit
+ *   fit = 1 - sqrt(max(0, ||T||^2 - ||G||^2)) / ||T||   (orthonormal factors).
+ * With opts.gauss_seidel = 0 every TTM-chain uses the input factors (Fig. 1 as
+ * printed); otherwise mode n uses the factors already refined in this call.
+ *   d_F   : host array of N device pointers, factors in (initial) and out (new).
+ *   d_G   : output core, prod K values.
+ *   h_fit : output fit (host double); may be NULL.  Synchronises when non-NULL.
+ */
+tucker_status hooi_iter(tucker_t t, void* const* d_F, void* d_G, double* h_fit, void* stream);
+
+/*
+ * ttm_chain_backward -- adjoint of ttm_chain.  For a cotangent dZ (R_n x
+ * Khat_n, compact rows as produced by ttm_chain):
+ *   dval(e)        = < dZ[row(l_n(e))], Kron_n(e) >
+ *   dF_m[l_m(e),:] += w(e) * dZ[row(l_n(e))] contracted with every other Kronecker row
+ * where w(e) is the tensor's value or d_vals[e].  The Kronecker rows are
+ * recomputed, never stored.
+ *   d_dF   : host array of N device pointers; entries are ACCUMULATED into
+ *            (caller zeroes them); a NULL entry (and entry `mode`) is skipped.
+ *   d_dval : output, nnz values in original element order; may be NULL.
+ */
+tucker_status ttm_chain_backward(tucker_t t, int mode, const void* const* d_F, const void* d_dZ,
+                                 const void* d_vals, void* const* d_dF, void* d_dval, void* stream);
+
+/*
+ * tucker_timings -- with opts.timing = 1, accumulated device milliseconds and
+ * launch counts per phase since the last reset, from CUDA events recorded on
+ * the launching stream.  Phases: 0 TTM-chain kernel, 1 split-slice fix-up,
+ * 2 Gram, 3 eigensolve, 4 back-projection + CholeskyQR2, 5 core + fit,
+ * 6 adjoint, 7 other.  ms[8] and launches[8] (either may be NULL); reset != 0
+ * clears the counters after reading.  Synchronises `stream`.
+ */
+tucker_status tucker_timings(tucker_t t, double* ms, int64_t* launches, int reset, void* stream);
+
+/* Bytes of device memory owned by the context (for reporting). */
+tucker_status tucker_memory(tucker_t t, int64_t* bytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUCKER_H */

@@ -1,0 +1,171 @@
+// Internal declarations shared by the libtucker translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tucker.h"
+
+#define TK_MAXN 6     // modes
+#define TK_MAXK 32    // core length per mode
+#define TK_MAXKHAT 4096
+
+// Row code stored per element of a mode-n copy: the compact row of its slice,
+// plus two flags for slices Lite splits over bins (Section 6.2: head / tail).
+#define TK_ROW_MASK 0x3FFFFFFFu
+#define TK_SPLIT_BIT 0x80000000u
+#define TK_HEAD_BIT 0x40000000u
+
+// Device error word bits.
+#define TK_DEV_ERR_INDEX 1
+#define TK_DEV_ERR_NUMERIC 2
+#define TK_DEV_ERR_NONFINITE 4
+#define TK_DEV_ERR_LIMIT 8
+
+enum tk_phase { PH_TTM = 0, PH_FIXUP, PH_GRAM, PH_EIG, PH_BACKPROJ, PH_CORE, PH_BWD, PH_OTHER, PH_COUNT };
+
+struct tk_status_error {
+  tucker_status code;
+  std::string msg;
+};
+
+// One mode's Lite partition and permuted copy, laid out "warp-interleaved":
+// bin p's k-th element lives at ((p / 32) * limit + k) * 32 + p % 32, so the
+// 32 bins of a warp read one contiguous 128-byte line per step.
+struct tk_mode {
+  int n = 0;
+  int P = 0;            // Lite bins
+  int Pa = 0;           // bins allocated: P rounded up to a multiple of 32 (extra bins empty)
+  int limit = 0;        // ceil(nnz / P)
+  int64_t cap = 0;      // Pa * limit slots per array
+  int R = 0;            // non-empty slices (compact rows)
+  int t_hat = 0;        // first stage-2 slice in sorted order
+  int nsplit = 0;       // stage-2 (split) slices
+  int Khat = 0;
+  int G = 1;            // column groups of the TTM-chain tile
+  int64_t E_max = 0, R_sum = 0, R_max = 0;
+  // permuted copy
+  uint32_t* rowcode = nullptr;
+  int32_t* oidx[TK_MAXN - 1] = {};
+  void* val = nullptr;
+  int32_t* perm = nullptr;
+  int32_t* bin_len = nullptr;
+  int32_t* row_id = nullptr;    // R slice ids
+  // split-slice fix-up tables
+  int32_t* split_row = nullptr;   // nsplit compact rows
+  int32_t* split_bhead = nullptr; // nsplit
+  int32_t* gap2 = nullptr;        // P stage-2 gap per bin
+  int nchunks = 0;
+  int32_t* chunk_split = nullptr;  // nchunks
+  int32_t* chunk_b0 = nullptr;     // nchunks (inclusive)
+  int32_t* chunk_b1 = nullptr;     // nchunks (exclusive)
+  int32_t* split_chunk0 = nullptr; // nsplit + 1
+};
+
+struct tk_buf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct tucker_ctx {
+  int N = 0;
+  int64_t L[TK_MAXN] = {};
+  int32_t K[TK_MAXN] = {};
+  int64_t nnz = 0;
+  int prec = TUCKER_FP32;
+  size_t esz = 4;
+  int gauss_seidel = 0;
+  int timing = 0;
+  int sm_count = 0;
+  double normT2 = 0.0;
+  tk_mode mode[TK_MAXN];
+  // library-owned device memory (everything allocated at init)
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  // factor buffers, padded leading dimension ldF[m]
+  int ldF[TK_MAXN] = {};
+  void* Fa[TK_MAXN] = {};   // current factors
+  void* Fb[TK_MAXN] = {};   // new factors
+  // workspace
+  void* Z = nullptr;        // max_n R_n * Khat_n
+  void* Zpart = nullptr;    // max_n 2 * P_n * Khat_n
+  double* Zchunk = nullptr; // max_n nchunks * Khat_n
+  void* Wpart = nullptr;    // Gram split partials
+  size_t Wpart_elems = 0;
+  double* W = nullptr;      // Khat x Khat
+  int2* gram_tiles = nullptr; // upper-triangle tile list
+  int gram_tiles_cap = 0;
+  double* eigX = nullptr;   // 2 x Khat x Kmax (eigensolver scratch)
+  void* Vs = nullptr;       // Khat x Kmax (T): V Sigma^-1
+  double* V = nullptr;      // Khat x Kmax (eigenvectors)
+  double* sigma = nullptr;  // Kmax
+  void* eigA = nullptr;     // Jacobi work matrix (T) Khat x Khat
+  void* eigV = nullptr;     // Jacobi vectors (T) Khat x Khat
+  void* U = nullptr;        // max R_n * Kmax (T)
+  double* Cpart = nullptr;  // blocks * Kmax^2
+  double* Rinv = nullptr;   // Kmax^2 x 2
+  double* colbest = nullptr;// blocks * Kmax * 2 (value, row) candidates
+  double* Gpart = nullptr;  // core partials
+  double* Gd = nullptr;     // core (double) prod K
+  double* fit_d = nullptr;  // [0] = ||G||^2, [1] = fit
+  int* err = nullptr;       // device error word
+  int maxR = 0, maxKhat = 0, Kmax = 0;
+  int64_t Gsize = 1;
+  // timing
+  cudaEvent_t ev[2 * 1024];
+  int ev_used = 0;
+  int ev_phase[1024];
+  double ms[PH_COUNT] = {};
+  int64_t launches[PH_COUNT] = {};
+  std::string last_error;
+};
+
+// ---- helpers implemented in tk_api.cu ----
+void tk_throw(tucker_status code, const std::string& msg);
+void tk_check_cuda(cudaError_t e, const char* what);
+void* tk_alloc(tucker_ctx* c, size_t bytes);
+void tk_phase_begin(tucker_ctx* c, int phase, cudaStream_t s);
+void tk_phase_end(tucker_ctx* c, cudaStream_t s);
+void tk_launched(tucker_ctx* c, int phase, int n = 1);
+int tk_sm_count();
+
+// ---- scan / sort (tk_scan_sort.cu) ----
+// exclusive prefix sum of n values; out may alias in. tmp is scratch from tk_scan_tmp_bytes.
+size_t tk_scan_tmp_bytes(int64_t n, size_t esz);
+void tk_exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, void* tmp, cudaStream_t s);
+void tk_exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, void* tmp, cudaStream_t s);
+// stable LSD radix sort of (key, value) pairs on the low `bits` bits of the keys.
+size_t tk_sort_tmp_bytes(int64_t n);
+void tk_radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_alt, int32_t* vals_alt, int64_t n,
+                         int bits, void* tmp, cudaStream_t s, uint32_t** keys_out, int32_t** vals_out);
+
+// ---- partition (tk_partition.cu) ----
+void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const void* d_val, int P,
+                       cudaStream_t s);
+void tk_partition_export(tucker_ctx* c, int n, int64_t* d_bin_ptr, int32_t* d_perm, cudaStream_t s);
+
+// ---- TTM-chain (tk_ttmc.cu) ----
+int tk_ttmc_groups(const tucker_ctx* c, int n);
+int tk_ttmc_threads_per_sm(const tucker_ctx* c, int n);
+void tk_ttmc_forward(tucker_ctx* c, int n, void* const* F, const int* ldF, const void* vals_override, void* Z,
+                     cudaStream_t s);
+void tk_ttmc_backward(tucker_ctx* c, int n, void* const* F, const int* ldF, const void* dZ,
+                      const void* vals_override, void* const* dF, void* dval, cudaStream_t s);
+
+// ---- factor update (tk_factor.cu) ----
+void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, double* sigma_out,
+                      cudaStream_t s);
+
+// ---- core / fit (tk_core.cu) ----
+void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s);
+double tk_norm2(tucker_ctx* c, const void* vals, int64_t n, cudaStream_t s);
+
+// ---- small device utilities ----
+void tk_copy_factor(tucker_ctx* c, const void* src, int lds, void* dst, int ldd, int64_t rows, int cols,
+                    cudaStream_t s);
+
+#define TK_CUDA(x) tk_check_cuda((x), #x)
+
+static inline __host__ __device__ int64_t tk_ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -1,0 +1,183 @@
+// New core G = T x_1 F_1^T ... x_N F_N^T (Fig. 1), computed as
+// G_(n*) = F_n*^T Z_(n*) from the compact penultimate matrix of one mode, then
+// folded to the first-mode-fastest layout; ||G||^2 and the fit in FP64.
+#include <algorithm>
+
+#include "tk_common.cuh"
+
+namespace {
+
+__device__ double block_sum_fixed(double v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+
+// Gpart[split][k][c] = sum over the split's rows r of F[row_id[r]][k] * Z[r][c].
+// Thread owns column c; rows in batches of 32 (factor rows staged in shared
+// memory), batch sums in T added into FP64 accumulators.
+template <typename T, int KM>
+__global__ void __launch_bounds__(128) k_core_partial(const T* __restrict__ Z, int R, int Khat,
+                                                      const int32_t* __restrict__ row_id, const T* __restrict__ F,
+                                                      int ldF, int K, int rows_per_split, double* __restrict__ Gpart) {
+  __shared__ T fr[32][KM];
+  const int c = blockIdx.x * 128 + threadIdx.x;
+  const int sp = blockIdx.y;
+  const int r0 = sp * rows_per_split, r1 = min(R, r0 + rows_per_split);
+  double dacc[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) dacc[k] = 0.0;
+  for (int rb = r0; rb < r1; rb += 32) {
+    for (int i = threadIdx.x; i < 32 * KM; i += 128) {
+      const int r = i / KM, k = i - r * KM;
+      fr[r][k] = (rb + r < r1 && k < K) ? F[(int64_t)row_id[rb + r] * ldF + k] : T(0);
+    }
+    __syncthreads();
+    if (c < Khat) {
+      T acc[KM];
+#pragma unroll
+      for (int k = 0; k < KM; ++k) acc[k] = T(0);
+      const int nr = min(32, r1 - rb);
+      for (int r = 0; r < nr; ++r) {
+        const T z = Z[(int64_t)(rb + r) * Khat + c];
+#pragma unroll
+        for (int k = 0; k < KM; ++k) acc[k] = fma(fr[r][k], z, acc[k]);
+      }
+#pragma unroll
+      for (int k = 0; k < KM; ++k) dacc[k] += (double)acc[k];
+    }
+    __syncthreads();
+  }
+  if (c < Khat)
+    for (int k = 0; k < K; ++k) Gpart[((int64_t)sp * K + k) * Khat + c] = dacc[k];
+}
+
+struct FoldInfo {
+  int N, n, Kn, Khat;
+  int K[TK_MAXN];
+};
+
+// G (first mode fastest) from the split partials, ||G||^2 and the fit; one CTA.
+template <typename T>
+__global__ void __launch_bounds__(1024) k_core_final(const double* __restrict__ Gpart, int nsplit, FoldInfo fi,
+                                                     double normT2, double* __restrict__ Gd, T* __restrict__ Gout,
+                                                     double* __restrict__ fit_out) {
+  __shared__ double red[32];
+  int stride[TK_MAXN];
+  {
+    int s = 1;
+    for (int m = 0; m < fi.N; ++m) {
+      stride[m] = s;
+      s *= fi.K[m];
+    }
+  }
+  const int total = fi.Kn * fi.Khat;
+  double g2 = 0.0;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int k = idx / fi.Khat, c = idx - k * fi.Khat;
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) s += Gpart[((int64_t)sp * fi.Kn + k) * fi.Khat + c];
+    int lin = k * stride[fi.n];
+    int rem = c;
+    for (int m = 0; m < fi.N; ++m) {
+      if (m == fi.n) continue;
+      lin += (rem % fi.K[m]) * stride[m];
+      rem /= fi.K[m];
+    }
+    Gd[lin] = s;
+    if (Gout) Gout[lin] = (T)s;
+    g2 += s * s;
+  }
+  g2 = block_sum_fixed(g2, red);
+  if (threadIdx.x == 0) {
+    fit_out[0] = g2;
+    fit_out[1] = 1.0 - sqrt(fmax(0.0, normT2 - g2)) / sqrt(normT2);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_norm2_partial(const T* __restrict__ v, int64_t n, double* part, int* err) {
+  __shared__ double red[32];
+  double s = 0.0;
+  bool bad = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = (double)v[i];
+    if (!isfinite(x)) bad = true;
+    s = fma(x, x, s);
+  }
+  if (bad) atomicOr(err, TK_DEV_ERR_NONFINITE);
+  s = block_sum_fixed(s, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
+__global__ void k_sum_final(const double* part, int n, double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
+  s = block_sum_fixed(s, red);
+  if (threadIdx.x == 0) *out = s;
+}
+
+template <typename T>
+void core_impl(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s) {
+  // the mode with the smallest TTM-chain work (nnz * Khat) and then the fewest rows
+  int best = 0;
+  for (int n = 1; n < c->N; ++n) {
+    const tk_mode& a = c->mode[n];
+    const tk_mode& b = c->mode[best];
+    if (a.Khat < b.Khat || (a.Khat == b.Khat && a.R < b.R)) best = n;
+  }
+  const int n = best;
+  const tk_mode& md = c->mode[n];
+  tk_ttmc_forward(c, n, F, ldF, nullptr, c->Z, s);
+  tk_phase_begin(c, PH_CORE, s);
+  const int K = c->K[n], Khat = md.Khat, R = md.R;
+  const int cb = (int)tk_ceil_div(Khat, 128);
+  int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), tk_ceil_div(4 * c->sm_count, cb)));
+  const int rps = (int)tk_ceil_div(R, nsplit);
+  dim3 grid(cb, nsplit);
+  const T* Z = (const T*)c->Z;
+  const T* Fn = (const T*)F[n];
+  if (K <= 8) k_core_partial<T, 8><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
+  else if (K <= 16) k_core_partial<T, 16><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
+  else k_core_partial<T, 32><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
+  TK_CUDA(cudaGetLastError());
+  FoldInfo fi{};
+  fi.N = c->N;
+  fi.n = n;
+  fi.Kn = K;
+  fi.Khat = Khat;
+  for (int m = 0; m < c->N; ++m) fi.K[m] = c->K[m];
+  k_core_final<T><<<1, 1024, 0, s>>>(c->Gpart, nsplit, fi, c->normT2, c->Gd, (T*)G_out, c->fit_d);
+  TK_CUDA(cudaGetLastError());
+  tk_launched(c, PH_CORE, 2);
+  tk_phase_end(c, s);
+}
+
+}  // namespace
+
+void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s) {
+  if (c->prec == TUCKER_FP32) core_impl<float>(c, F, ldF, G_out, s);
+  else core_impl<double>(c, F, ldF, G_out, s);
+}
+
+double tk_norm2(tucker_ctx* c, const void* vals, int64_t n, cudaStream_t s) {
+  const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(n, 256), 4 * c->sm_count));
+  double* part = nullptr;
+  TK_CUDA(cudaMalloc(&part, (size_t)(nb + 1) * sizeof(double)));
+  if (c->prec == TUCKER_FP32) k_norm2_partial<float><<<nb, 256, 0, s>>>((const float*)vals, n, part, c->err);
+  else k_norm2_partial<double><<<nb, 256, 0, s>>>((const double*)vals, n, part, c->err);
+  k_sum_final<<<1, 256, 0, s>>>(part, nb, part + nb);
+  double out = 0.0;
+  TK_CUDA(cudaMemcpyAsync(&out, part + nb, sizeof(double), cudaMemcpyDeviceToHost, s));
+  TK_CUDA(cudaStreamSynchronize(s));
+  cudaFree(part);
+  return out;
+}

@@ -1,0 +1,168 @@
+"""GPU parity of the factor update (Fig. 1 "SVD"), the core and whole HOOI
+invocations (Fig. 1) through the C ABI, against the FP64 oracle.
+
+Tolerances (from the method's acceptance bounds): factor subspaces by
+projector distance <= 1e-4 in the FP32 context (1e-9 in FP64), fit within
+1e-6 of the oracle (1e-10 in FP64)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import tucker_oracle as O
+from paper_1804_09494_gb300 import synth
+from tests.gpu_cases import DT, NP, case, factors, make, rel_err
+
+pytestmark = pytest.mark.gpu
+
+PROJ = {"fp32": 1e-4, "fp64": 1e-9}
+FIT = {"fp32": 1e-6, "fp64": 1e-10}
+
+
+def to_np(t):
+    return t.double().cpu().numpy()
+
+
+def aligned_core(G, F, Fo, K):
+    """Flip the GPU core's signs column by column to the oracle factors' signs."""
+    Gt = G.reshape(K, order="F").copy()
+    for m, (f, fo) in enumerate(zip(F, Fo)):
+        s = np.sign(np.sum(f * fo, axis=0))
+        s[s == 0] = 1
+        Gt = np.moveaxis(np.moveaxis(Gt, m, -1) * s, -1, m)
+    return Gt.reshape(-1, order="F")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("L,nnz,zipf,K", [((200, 150, 100), 20_000, None, (8, 8, 8)),
+                                         ((3000, 2000, 500), 200_000, (1.1, 1.1, 1.1), (10, 10, 10)),
+                                         ((400, 300, 60, 20), 100_000, (1.2, 1.2, None, None), (6, 5, 4, 3))])
+def test_factor_update_matches_oracle(L, nnz, zipf, K, prec):
+    c = case(L, nnz, zipf, "lognormal", seed=31)
+    tk = make(c, K, prec)
+    _, Fo = factors(L, K, 7, prec)
+    for n in range(len(L)):
+        Zo = O.ttm_chain(L, c["idx"], c["vals"].astype(np.float64), Fo, n)
+        rid = np.flatnonzero(np.bincount(c["idx"][n], minlength=L[n]) > 0)
+        Zc = Zo[rid].astype(NP[prec]).astype(np.float64)
+        Zfull = np.zeros_like(Zo)
+        Zfull[rid] = Zc
+        F, sigma = tk.factor_update(n, torch.from_numpy(Zc).to(DT[prec]).cuda())
+        torch.cuda.synchronize()
+        Uo, so = O.leading_left_singular_vectors(Zfull, K[n])
+        Fg = to_np(F)
+        assert O.projector_distance(Fg, Uo) <= PROJ[prec], n
+        assert rel_err(sigma.cpu().numpy(), so) <= (1e-5 if prec == "fp32" else 1e-11)
+        orth = 1e-5 if prec == "fp32" else 1e-12
+        assert np.abs(Fg.T @ Fg - np.eye(K[n])).max() <= orth
+        empty = np.setdiff1d(np.arange(L[n]), rid)
+        assert not np.any(Fg[empty])
+        for k in range(K[n]):  # sign rule: largest-magnitude entry positive
+            assert Fg[np.argmax(np.abs(Fg[:, k])), k] > 0
+    tk.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_core_matches_oracle(prec):
+    c = case((300, 200, 100), 40_000, (1.1, 1.1, 1.1), "uniform", seed=32)
+    K = (8, 6, 5)
+    tk = make(c, K, prec)
+    Fd, Fo = factors(c["L"], K, 2, prec)
+    G = tk.core(Fd)
+    torch.cuda.synchronize()
+    Go = O.core(c["L"], c["idx"], c["vals"].astype(np.float64), Fo)
+    assert rel_err(to_np(G), Go) <= (1e-5 if prec == "fp32" else 1e-12)
+    tk.close()
+
+
+def _run_hooi(c, K, F0, iters, prec, gauss_seidel=False):
+    tk = make(c, K, prec, gauss_seidel=gauss_seidel)
+    F = [torch.from_numpy(np.ascontiguousarray(f, dtype=NP[prec])).cuda() for f in F0]
+    fits = []
+    for _ in range(iters):
+        G, fit = tk.hooi_iter(F)
+        fits.append(fit)
+    out = ([to_np(f) for f in F], to_np(G), fits)
+    tk.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_hooi_uniform_config_hosvd_init(prec):
+    """3-mode 200x150x100, 20,000 uniform distinct nonzeros, core 8^3, HOSVD
+    bootstrap, 5 invocations."""
+    w = synth.workload("uniform-200x150x100-nnz20k-k8")
+    c = dict(L=w["L"], idx=w["idx"], vals=w["vals"])
+    K = w["K"]
+    F0 = O.hosvd_init(c["L"], c["idx"], c["vals"].astype(np.float64), K)
+    F0 = [np.ascontiguousarray(f.astype(NP[prec]).astype(np.float64)) for f in F0]
+    F, G, fits = _run_hooi(c, K, F0, 5, prec)
+    Fo, Go, fito = O.hooi(c["L"], c["idx"], c["vals"].astype(np.float64), F0, iters=5)
+    for m in range(3):
+        assert O.projector_distance(F[m], Fo[m]) <= PROJ[prec], m
+    assert abs(fits[-1] - fito) <= FIT[prec]
+    assert rel_err(aligned_core(G, F, Fo, K), Go) <= (1e-4 if prec == "fp32" else 1e-9)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("L,nnz,zipf,K", [((3000, 2000, 500), 200_000, (1.1, 1.1, 1.1), (10, 10, 10)),
+                                         ((500, 500, 80, 30), 80_000, (1.3, 1.3, 1.3, 1.3), (8, 8, 8, 8))])
+def test_hooi_zipf_random_init(L, nnz, zipf, K, prec):
+    c = case(L, nnz, zipf, "lognormal", seed=33)
+    _, F0 = factors(L, K, 11, prec)
+    iters = 3
+    F, G, fits = _run_hooi(c, K, F0, iters, prec)
+    Fo = [f.copy() for f in F0]
+    for it in range(iters):
+        Fo = O.hooi_invocation(L, c["idx"], c["vals"].astype(np.float64), Fo)
+    Go = O.core(L, c["idx"], c["vals"].astype(np.float64), Fo)
+    fito = O.fit(c["vals"].astype(np.float64), Go)
+    for m in range(len(L)):
+        assert O.projector_distance(F[m], Fo[m]) <= PROJ[prec], m
+    assert abs(fits[-1] - fito) <= FIT[prec]
+    assert rel_err(aligned_core(G, F, Fo, K), Go) <= (1e-4 if prec == "fp32" else 1e-9)
+
+
+def test_hooi_gauss_seidel_variant_fp64():
+    c = case((300, 250, 200), 30_000, (1.1, 1.1, 1.1), "uniform", seed=34)
+    K = (5, 4, 6)
+    _, F0 = factors(c["L"], K, 12, "fp64")
+    F, G, fits = _run_hooi(c, K, F0, 2, "fp64", gauss_seidel=True)
+    Fo, Go, fito = O.hooi(c["L"], c["idx"], c["vals"].astype(np.float64), F0, iters=2, variant="gauss_seidel")
+    for m in range(3):
+        assert O.projector_distance(F[m], Fo[m]) <= PROJ["fp64"]
+    assert abs(fits[-1] - fito) <= FIT["fp64"]
+
+
+def test_hooi_exact_rank_recovery_fp64():
+    """A sparse tensor of exact multilinear rank is recovered exactly (fit 1)."""
+    rng = np.random.default_rng(5)
+    L, K, live = (300, 250, 200), (3, 4, 2), (20, 15, 12)
+    A = []
+    for l, k, r in zip(L, K, live):
+        M = np.zeros((l, k))
+        M[rng.choice(l, size=r, replace=False)] = rng.standard_normal((r, k))
+        A.append(M)
+    T = rng.standard_normal(K)
+    for m in range(3):
+        T = np.moveaxis(np.tensordot(T, A[m], axes=([m], [1])), -1, m)
+    idx = np.array(np.nonzero(T)).astype(np.int32)
+    c = dict(L=L, idx=idx, vals=T[tuple(idx)])
+    _, F0 = factors(L, K, 3, "fp64")
+    tk = make(c, K, "fp64")
+    F = [torch.from_numpy(f).cuda() for f in F0]
+    tk.hooi_iter(F)
+    G, fit = tk.hooi_iter(F)
+    assert abs(fit - 1.0) < 1e-6  # the ||T||^2 - ||G||^2 identity is sqrt(eps)-accurate at fit = 1
+    for m in range(3):
+        Q, _ = np.linalg.qr(A[m])
+        assert O.projector_distance(to_np(F[m]), Q) < 1e-9
+    tk.close()
+
+
+def test_mixed_and_fp64_forms_reach_the_same_fit():
+    c = case((3000, 2000, 500), 200_000, (1.1, 1.1, 1.1), "lognormal", seed=35)
+    K = (10, 10, 10)
+    _, F0 = factors(c["L"], K, 13, "fp32")
+    _, _, f32 = _run_hooi(c, K, F0, 3, "fp32")
+    _, _, f64 = _run_hooi(c, K, F0, 3, "fp64")
+    assert abs(f32[-1] - f64[-1]) <= 1e-6
