@@ -96,10 +96,17 @@ def leading_left_singular_vectors(Z, K):
     """F~_n <- leading K left singular vectors of Z_(n) (Fig. 1, SVD step).
 
     Uses the library SVD as the step; columns ordered by descending singular
-    value and sign-normalised.  Returns (U, sigma)."""
+    value and sign-normalised.  Rows of empty slices are zero (Section 3: the
+    truncated copy omits them) and the SVD of [A; 0] is [U_A; 0], so the SVD
+    is taken over the non-empty rows only.  Returns (U, sigma)."""
     Z = np.asarray(Z, dtype=np.float64)
-    U, s, _ = np.linalg.svd(Z, full_matrices=False)
-    return sign_normalise(U[:, :K]), s[:K].copy()
+    nz = np.flatnonzero(np.any(Z != 0.0, axis=1))
+    if len(nz) < K:
+        nz = np.arange(Z.shape[0])
+    Uc, s, _ = np.linalg.svd(Z[nz], full_matrices=False)
+    U = np.zeros((Z.shape[0], K))
+    U[nz] = Uc[:, :K]
+    return sign_normalise(U), s[:K].copy()
 
 
 def hooi_invocation(L, idx, vals, F, K=None, variant="jacobi"):
