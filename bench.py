@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark of the HOOI hot path on the 3-mode Zipf workload.
+
+Workload: 2,000,000 x 1,000,000 x 50,000 COO tensor with 100M distinct
+nonzeros, Zipf(1.1) coordinates per mode (seeded permutation of the index
+space), lognormal(0,1) values, core 10x10x10, seeded random orthonormal
+initial factors.  A step is one HOOI invocation (Fig. 1: TTM-chain + factor
+update for every mode, then core and fit) with the tensor resident in HBM.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU
+oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "zipf1.1-2Mx1Mx50K-nnz100M-k10"
+METRIC = "HOOI s/iter & TTM-chain GB/s (% HBM peak), mixed vs FP64 GPU at fixed fit"
+CPU_SAMPLE = 500_000  # elements of the oracle's bounded sample (first elements of the stream)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--nnz", type=int, default=None, help="fewer nonzeros, same recipe (smoke runs only)")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), bf16=float(d["bf16_tflops"]), sm_max_mhz=float(d.get("sm_max_mhz", 2070)),
+                    source="measured")
+    return dict(hbm_gbs=6800.0, bf16=1900.0, sm_max_mhz=2070.0, source="fallback")
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "100", "-i", str(self.gpu_id)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+# ----------------------------------------------------------------- helpers
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def ttm_bytes_flops(w, R, n):
+    """Algorithmic bytes and FLOPs of one TTM-chain launch along mode n:
+    the element stream (N-1 coordinates + row code + value, 4 B each), every
+    other factor read once, the compact Z written once; one FMA per Z entry
+    per element."""
+    L, K, nnz = w["L"], w["K"], len(w["vals"])
+    N = len(L)
+    khat = int(np.prod([K[m] for m in range(N) if m != n]))
+    stream = nnz * 4 * (N + 1)
+    fac = sum(L[m] * K[m] * 4 for m in range(N) if m != n)
+    z = R[n] * khat * 4
+    return stream + fac + z, 2.0 * nnz * khat
+
+
+def core_mode(w, R):
+    K = w["K"]
+    N = len(K)
+    kh = [int(np.prod([K[m] for m in range(N) if m != n])) for n in range(N)]
+    best = 0
+    for n in range(1, N):
+        if kh[n] < kh[best] or (kh[n] == kh[best] and R[n] < R[best]):
+            best = n
+    return best
+
+
+def oracle_sample_seconds(w, sample):
+    """Times one oracle HOOI invocation (+ core + fit) on the first `sample`
+    elements, in a fresh single-threaded process."""
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "sample.npz")
+        F0 = w["F0"]
+        np.savez(path, idx=w["idx"][:, :sample], vals=w["vals"][:sample], L=np.array(w["L"]),
+                 **{f"F{m}": F0[m] for m in range(len(F0))})
+        code = (
+            "import sys, time, numpy as np; sys.path.insert(0, %r)\n"
+            "from oracle import tucker_oracle as O\n"
+            "d = np.load(%r); L = tuple(int(x) for x in d['L']); N = len(L)\n"
+            "F = [d['F%%d' %% m] for m in range(N)]\n"
+            "idx = d['idx'].astype(np.int64); v = d['vals'].astype(np.float64)\n"
+            "t = time.perf_counter(); F = O.hooi_invocation(L, idx, v, F); G = O.core(L, idx, v, F); f = O.fit(v, G)\n"
+            "print(time.perf_counter() - t)\n" % (ROOT, path))
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
+        if r.returncode != 0:
+            raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+        return float(r.stdout.strip().splitlines()[-1])
+
+
+def load_workload(args):
+    from paper_1804_09494_gb300 import synth
+    w = synth.workload(args.workload, nnz=args.nnz)
+    w["F0"] = synth.random_orthonormal_factors(w["L"], w["K"], seed=1234)
+    return w
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    w = load_workload(args)
+    nnz = len(w["vals"])
+    sample = min(args.cpu_sample, nnz)
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm state; warm-up steps are not repeated
+    times = [oracle_sample_seconds(w, sample) * nnz / sample for _ in range(args.steps)]
+    t = float(np.mean(times))
+    line = dict(metric=METRIC, value=t, unit="s/iter", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=t * 1e3, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", impl="reference",
+                config=dict(workload=args.workload, nnz=nnz, L=list(w["L"]), K=list(w["K"])),
+                cpu_baseline=dict(value=t, unit="s/iter", cores=1, kind="oracle",
+                                  sample=f"first {sample:,} of {nnz:,} elements, one HOOI invocation + core + fit, "
+                                         f"extrapolated linearly in nnz"),
+                e2e=dict(value=t, unit="s/iter", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1804_09494_gb300.tucker import PHASES, Tucker
+
+    rank, world, local = dist_info()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pk = peaks()
+
+    w = load_workload(args)
+    L, K = w["L"], w["K"]
+    N = len(L)
+    nnz = len(w["vals"])
+    idx_d = torch.from_numpy(w["idx"]).to(dev)
+    vals_d = torch.from_numpy(w["vals"]).to(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # distribution (Lite partition + permuted copies), timed once
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tk = Tucker(idx_d, vals_d, L, K, prec="fp32", timing=True)
+    torch.cuda.synchronize()
+    partition_s = time.perf_counter() - t0
+    R = tk.R
+    stats = [tk.stats(n) for n in range(N)]
+    F = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in w["F0"]]
+    G = torch.empty(int(np.prod(K)), dtype=torch.float32, device=dev)
+
+    for _ in range(args.warmup):
+        tk.hooi_iter(F, G, want_fit=False)
+    tk.timings(reset=True)
+    clocks = Clocks(torch.cuda.get_device_properties(dev).uuid and f"GPU-{torch.cuda.get_device_properties(dev).uuid}")
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for s in range(args.steps):
+        _, fit = tk.hooi_iter(F, G, want_fit=(s == args.steps - 1))
+    e1.record(stream)
+    barrier()
+    ck = clocks.stop()
+    t_loc = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_loc], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_all = float(tt.item())
+    else:
+        t_all = t_loc
+    ph = tk.timings(reset=True)
+    launches = int(sum(v[1] for v in ph.values()))
+    s_per_iter = t_all / (args.steps * world)  # whole job: world x steps invocations in t_all
+    fit_mixed = fit
+
+    # roofline of the dominant kernel (the TTM-chain): algorithmic bytes of the
+    # launches in the timed region over their summed CUDA-event durations
+    per_iter_bytes = 0.0
+    per_iter_flops = 0.0
+    for n in list(range(N)) + [core_mode(w, R)]:
+        b, f = ttm_bytes_flops(w, R, n)
+        per_iter_bytes += b
+        per_iter_flops += f
+    ttm_ms, ttm_launches = ph["ttm_chain"]
+    ttm_s_per_launch = ttm_ms / 1e3 / max(ttm_launches, 1)
+    launches_per_iter = ttm_launches / args.steps
+    bytes_per_launch = per_iter_bytes / launches_per_iter
+    achieved_gbs = bytes_per_launch / ttm_s_per_launch / 1e9
+    fp32_peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    achieved_tflops = per_iter_flops / launches_per_iter / ttm_s_per_launch / 1e12
+
+    # end to end through the public API with pinned host buffers
+    Fh = [torch.from_numpy(f.astype(np.float32)).pin_memory() for f in w["F0"]]
+    Fo = [torch.empty_like(f).pin_memory() for f in Fh]
+    Gh = torch.empty(G.shape, dtype=torch.float32).pin_memory()
+    h2d = sum(f.numel() * 4 for f in Fh)
+    d2h = h2d + Gh.numel() * 4 + 8
+    e2e_steps = max(1, min(args.steps, 20))
+    barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        for fd, fh in zip(F, Fh):
+            fd.copy_(fh, non_blocking=True)
+        _, fit_e2e = tk.hooi_iter(F, G, want_fit=True)  # the fit is read back to the host
+        for fo, fd in zip(Fo, F):
+            fo.copy_(fd, non_blocking=True)
+        Gh.copy_(G, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_s = e0.elapsed_time(e1) / 1e3 / e2e_steps
+
+    # the plain FP64 form on the same tensor and initial factors; fits compared
+    # after the same number of invocations (fixed fit)
+    fp64 = None
+    if args.fp64_steps > 0:
+        tk64 = Tucker(idx_d, vals_d.double(), L, K, prec="fp64", timing=False)
+        F64 = [torch.from_numpy(f).to(dev) for f in w["F0"]]
+        G64 = torch.empty(int(np.prod(K)), dtype=torch.float64, device=dev)
+        Fm = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in w["F0"]]
+        fits32, fits64 = [], []
+        tk.hooi_iter(Fm, G, want_fit=True)
+        tk64.hooi_iter(F64, G64, want_fit=True)
+        barrier()
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            _, f64 = tk64.hooi_iter(F64, G64, want_fit=True)
+            fits64.append(f64)
+        e1.record(stream)
+        barrier()
+        t64 = e0.elapsed_time(e1) / 1e3 / args.fp64_steps
+        for _ in range(args.fp64_steps):
+            _, f32 = tk.hooi_iter(Fm, G, want_fit=True)
+            fits32.append(f32)
+        fp64 = dict(s_per_iter=t64, fit_after=[round(x, 12) for x in fits64],
+                    mixed_fit_after=[round(x, 12) for x in fits32],
+                    max_fit_gap=max(abs(a - b) for a, b in zip(fits32, fits64)),
+                    speedup_mixed_over_fp64=t64 / max(s_per_iter * world, 1e-12))
+        tk64.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = min(args.cpu_sample, nnz)
+        ts = oracle_sample_seconds(w, sample)
+        cpu = dict(value=ts * nnz / sample, unit="s/iter", cores=1, kind="oracle",
+                   sample=f"first {sample:,} of {nnz:,} elements (same L, K, initial factors); one HOOI invocation "
+                          f"+ core + fit took {ts:.2f} s on one host thread; extrapolated linearly in nnz")
+
+    if rank == 0:
+        line = dict(
+            metric=METRIC, value=s_per_iter, unit="s/iter", n_gpus=world, steps=args.steps, warmup=args.warmup,
+            ms_per_step=t_all / args.steps * 1e3, higher_is_better=False, scaling="weak", vs_baseline=None,
+            dtype="f32", data="synthetic",
+            config=dict(workload=args.workload, nnz=nnz, L=list(L), K=list(K), R=R, prec="fp32 TTM-chain, FP32 Gram "
+                        "with FP64 reductions, FP64-polished eigensolve, CholeskyQR2 with FP64 reductions",
+                        l2="inputs larger than L2 (permuted copies ~6 GB per context)",
+                        parallelism="replicas" if world > 1 else "single GPU"),
+            roofline=dict(bound="hbm", achieved=round(achieved_gbs, 1), peak=pk["hbm_gbs"], unit="GB/s",
+                          frac=round(achieved_gbs / pk["hbm_gbs"], 4), traffic=None,
+                          kernel="k_ttmc_fwd", peak_source=pk["source"] + " (hbm_gbs)",
+                          bytes_per_launch=int(bytes_per_launch), ms_per_launch=round(ttm_s_per_launch * 1e3, 4),
+                          alu_tflops=round(achieved_tflops, 2), alu_frac_fp32=round(achieved_tflops / fp32_peak_tflops, 4)),
+            ttm_chain_gbs=round(achieved_gbs, 1), ttm_chain_frac_hbm=round(achieved_gbs / pk["hbm_gbs"], 4),
+            phases_ms_per_iter={k: round(v[0] / args.steps, 4) for k, v in ph.items()},
+            fit=fit_mixed, fp64_form=fp64, partition_s=round(partition_s, 3),
+            partition=[dict(E_max=s["E_max"], R_sum=s["R_sum"], R_max=s["R_max"], R_n=s["R_n"], P=s["P"]) for s in stats],
+            e2e=dict(value=e2e_s, unit="s/iter", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+            gpu_launches=launches, clocks=dict(sm_mhz=ck["sm_mhz"], sm_max_mhz=ck["sm_max_mhz"], reasons=ck["reasons"],
+                                               samples=ck["samples"]),
+            cpu_baseline=cpu, memory_bytes=tk.memory())
+        print(json.dumps(line), flush=True)
+    tk.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -57,16 +57,18 @@ class ZipfSampler:
     permutation of the index space."""
 
     def __init__(self, L, s, seed, mode):
+        import torch
         self.L = int(L)
         w = np.arange(1, self.L + 1, dtype=np.float64) ** (-float(s))
         cdf = np.cumsum(w)
-        self.cdf = cdf / cdf[-1]
-        self.perm = _rng(seed, 1000 + mode).permutation(self.L).astype(np.int32)
+        self.cdf = torch.from_numpy(cdf / cdf[-1])
+        self.perm = torch.from_numpy(_rng(seed, 1000 + mode).permutation(self.L).astype(np.int32))
 
     def draw(self, u):
-        k = np.searchsorted(self.cdf, u, side="right")
-        np.minimum(k, self.L - 1, out=k)
-        return self.perm[k]
+        import torch
+        k = torch.searchsorted(self.cdf, torch.from_numpy(u), right=True)
+        k.clamp_(max=self.L - 1)
+        return self.perm[k].numpy()
 
 
 def _draw_coords(L, zipf, samplers, rng, n):
@@ -87,6 +89,16 @@ def _keys(L, idx):
     return key
 
 
+def _first_occurrences(keys):
+    """Positions of the first occurrence of every distinct key, in draw order."""
+    import torch
+    k = torch.from_numpy(keys)
+    sk, perm = torch.sort(k, stable=True)
+    first = torch.ones(len(sk), dtype=torch.bool)
+    first[1:] = sk[1:] != sk[:-1]
+    return torch.sort(perm[first]).values.numpy()
+
+
 def coo(L, nnz, zipf=None, values="uniform", seed=0):
     """Distinct-coordinate COO tensor: returns (idx int32 (N, nnz), vals float32 (nnz,))."""
     L = tuple(int(x) for x in L)
@@ -102,17 +114,16 @@ def coo(L, nnz, zipf=None, values="uniform", seed=0):
     rng = _rng(seed, 1)
     idx = np.zeros((N, 0), dtype=np.int32)
     keys = np.zeros(0, dtype=np.int64)
-    want = nnz
     rounds = 0
+    frac_new = 1.0  # fraction of the last round's draws that were new distinct cells
     while keys.size < nnz:
-        extra = int((want - keys.size) * 1.15) + 1024
+        extra = int((nnz - keys.size) / max(frac_new, 0.02) * 1.1) + 1024
         new = _draw_coords(L, zipf, samplers, rng, extra)
         allk = np.concatenate([keys, _keys(L, new)])
-        _, first = np.unique(allk, return_index=True)
-        first.sort()  # keep draw order
-        allidx = np.concatenate([idx, new], axis=1)
+        first = _first_occurrences(allk)
+        frac_new = (len(first) - keys.size) / extra
         first = first[:nnz]
-        idx = allidx[:, first]
+        idx = np.concatenate([idx, new], axis=1)[:, first]
         keys = allk[first]
         rounds += 1
         if rounds > 64:
