@@ -11,6 +11,8 @@
 // block j0 of b, are fixed per column group g.  A whole slice is written to its
 // compact Z row once; a split piece goes to a per-bin partial slot and the
 // fix-up adds the pieces in bin order (deterministic, FP64 sums).
+#include <algorithm>
+
 #include "tk_common.cuh"
 
 namespace {
@@ -45,6 +47,7 @@ struct TtmcArgs {
   int KA, KB;
   int Khat;
   int store_vec;
+  int chunk;  // staged steps per buffer
   T* Z;
   T* Zpart;
   // adjoint
@@ -91,15 +94,59 @@ __device__ __forceinline__ void load_row(const T* __restrict__ row, int valid, T
   }
 }
 
+// ---------------------------------------------------------------- staging
+// Each warp streams the element arrays of its 32 bins through shared memory:
+// steps [k0, k0+C) of a warp occupy one contiguous span per array (the
+// warp-interleaved layout), copied with 16-byte cp.async into one of two
+// buffers while the other buffer is being consumed.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ void stage_span(void* sdst, const void* gsrc, int bytes, int lane) {
+#pragma unroll 1
+  for (int off = lane * 16; off < bytes; off += 32 * 16) cp_async16((char*)sdst + off, (const char*)gsrc + off);
+}
+
+// One staging buffer of C steps: code[C*32], oidx_q[C*32] (q < nother),
+// then val[C*32] (type T, if staged) and perm[C*32] (if staged).
+template <typename T>
+__host__ __device__ inline int stage_bytes(int C, int nother, bool val, bool perm) {
+  return C * 32 * (4 * (1 + nother) + (val ? (int)sizeof(T) : 0) + (perm ? 4 : 0));
+}
+
+template <typename T>
+__device__ __forceinline__ void issue_chunk(const TtmcArgs<T>& a, char* buf, int CW, int64_t wbase, int k0, int ns,
+                                            int lane, bool val, bool perm) {
+  const int64_t off = (wbase + k0) * 32;
+  const int b4 = ns * 32 * 4;
+  uint32_t* w = (uint32_t*)buf;
+  stage_span(w, a.rowcode + off, b4, lane);
+#pragma unroll 1
+  for (int q = 0; q < a.nother; ++q) stage_span(w + (1 + q) * CW, a.oidx[q] + off, b4, lane);
+  char* vb = (char*)(w + (1 + a.nother) * CW);
+  if (val) {
+    stage_span(vb, a.val + off, ns * 32 * (int)sizeof(T), lane);
+    vb += (size_t)CW * sizeof(T);
+  }
+  if (perm) stage_span(vb, a.perm + off, b4, lane);
+}
+
 template <typename T, int MA, int MB, bool EA, bool EB>
 __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
-  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int g = (int)(gw % a.G);
   const int64_t bw = gw / a.G;
   if (bw * 32 >= a.P) return;
   const int bin = (int)(bw * 32 + lane);
   const int len = a.bin_len[bin];
+  const int wlen = __reduce_max_sync(0xffffffffu, len);
   const int ka = EA ? MA : a.KA;
   const int jb = g % a.NB, o = g / a.NB;
   const int j0 = jb * a.TB;
@@ -113,7 +160,12 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
     }
   }
   const int colbase = a.KA * j0 + a.KA * a.KB * o;
-  const int64_t base = (int64_t)bw * a.limit * 32 + lane;
+  const int64_t wbase = bw * a.limit;
+  const int C = a.chunk;
+  const bool sval = a.vals_override == nullptr, sperm = !sval;
+  const int sb = stage_bytes<T>(C, a.nother, sval, sperm);
+  const int CW = C * 32;
+  char* wsm = smem + (size_t)wib * 2 * sb;
 
   T acc[MA * MB];
 #pragma unroll
@@ -137,46 +189,67 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
     }
   };
 
-  uint32_t cur = len > 0 ? a.rowcode[base] : 0u;
-  for (int k = 0; k < len; ++k) {
-    const int64_t pos = base + (int64_t)k * 32;
-    const uint32_t code = a.rowcode[pos];
-    if (code != cur) {
-      flush(cur);
+  const int nch = (wlen + C - 1) / C;
+  if (nch > 0) issue_chunk(a, wsm, CW, wbase, 0, min(C, wlen), lane, sval, sperm);
+  cp_commit();
+  if (nch > 1) issue_chunk(a, wsm + sb, CW, wbase, C, min(C, wlen - C), lane, sval, sperm);
+  cp_commit();
+  uint32_t cur = len > 0 ? a.rowcode[wbase * 32 + lane] : 0u;
+  for (int c = 0; c < nch; ++c) {
+    cp_wait_1();
+    __syncwarp();
+    const uint32_t* sw = (const uint32_t*)(wsm + (c & 1) * sb);
+    const T* sv = (const T*)(sw + (1 + a.nother) * CW);
+    const int32_t* sp = (const int32_t*)((const char*)sv + (sval ? (size_t)CW * sizeof(T) : 0));
+    const int ns = min(C, wlen - c * C);
+#pragma unroll 1
+    for (int j = 0; j < ns; ++j) {
+      if (c * C + j >= len) break;
+      const int sj = j * 32 + lane;
+      const uint32_t code = sw[sj];
+      if (code != cur) {
+        flush(cur);
 #pragma unroll
-      for (int i = 0; i < MA * MB; ++i) acc[i] = T(0);
-      cur = code;
+        for (int i = 0; i < MA * MB; ++i) acc[i] = T(0);
+        cur = code;
+      }
+      T v = sval ? sv[sj] : a.vals_override[sp[sj]];
+      for (int q = 2; q < a.nother; ++q) v *= __ldg(a.F[q] + (int64_t)(int32_t)sw[(1 + q) * CW + sj] * a.ld[q] + oc[q - 2]);
+      T fa[Row<T, MA>::R];
+      load_row<T, MA>(a.F[0] + (int64_t)(int32_t)sw[CW + sj] * a.ld[0], ka, fa);
+      T fb[Row<T, MB>::R];
+      if (a.nother >= 2) {
+        load_row<T, MB>(a.F[1] + (int64_t)(int32_t)sw[2 * CW + sj] * a.ld[1] + j0, tb, fb);
+      } else {
+#pragma unroll
+        for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
+      }
+#pragma unroll
+      for (int jj = 0; jj < MB; ++jj) {
+        const T t = v * fb[jj];
+#pragma unroll
+        for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(fa[i], t, acc[i + MA * jj]);
+      }
     }
-    T v = a.vals_override ? a.vals_override[a.perm[pos]] : a.val[pos];
-    for (int q = 2; q < a.nother; ++q) v *= __ldg(a.F[q] + (int64_t)a.oidx[q][pos] * a.ld[q] + oc[q - 2]);
-    T fa[Row<T, MA>::R];
-    load_row<T, MA>(a.F[0] + (int64_t)a.oidx[0][pos] * a.ld[0], ka, fa);
-    T fb[Row<T, MB>::R];
-    if (a.nother >= 2) {
-      load_row<T, MB>(a.F[1] + (int64_t)a.oidx[1][pos] * a.ld[1] + j0, tb, fb);
-    } else {
-#pragma unroll
-      for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
-    }
-#pragma unroll
-    for (int jj = 0; jj < MB; ++jj) {
-      const T t = v * fb[jj];
-#pragma unroll
-      for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(fa[i], t, acc[i + MA * jj]);
-    }
+    __syncwarp();
+    if (c + 2 < nch) issue_chunk(a, wsm + (c & 1) * sb, CW, wbase, (c + 2) * C, min(C, wlen - (c + 2) * C), lane, sval, sperm);
+    cp_commit();
   }
+  cp_wait_0();
   if (len > 0) flush(cur);
 }
 
 template <typename T, int MA, int MB, bool EA, bool EB>
 __global__ void __launch_bounds__(128) k_ttmc_bwd(const TtmcArgs<T> a) {
-  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) char smem[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int g = (int)(gw % a.G);
   const int64_t bw = gw / a.G;
   if (bw * 32 >= a.P) return;
   const int bin = (int)(bw * 32 + lane);
   const int len = a.bin_len[bin];
+  const int wlen = __reduce_max_sync(0xffffffffu, len);
   const int ka = EA ? MA : a.KA;
   const int jb = g % a.NB, o = g / a.NB;
   const int j0 = jb * a.TB;
@@ -190,83 +263,107 @@ __global__ void __launch_bounds__(128) k_ttmc_bwd(const TtmcArgs<T> a) {
     }
   }
   const int colbase = a.KA * j0 + a.KA * a.KB * o;
-  const int64_t base = (int64_t)bw * a.limit * 32 + lane;
+  const int64_t wbase = bw * a.limit;
+  const int C = a.chunk;
+  const bool sval = a.vals_override == nullptr;
+  const int sb = stage_bytes<T>(C, a.nother, sval, true);
+  const int CW = C * 32;
+  char* wsm = smem + (size_t)wib * 2 * sb;
 
   T D[MA * MB];
   uint32_t cur = 0xFFFFFFFFu;
-  for (int k = 0; k < len; ++k) {
-    const int64_t pos = base + (int64_t)k * 32;
-    const uint32_t code = a.rowcode[pos];
-    if (code != cur) {
-      const T* src = a.dZ + (int64_t)(code & TK_ROW_MASK) * a.Khat + colbase;
+  const int nch = (wlen + C - 1) / C;
+  if (nch > 0) issue_chunk(a, wsm, CW, wbase, 0, min(C, wlen), lane, sval, true);
+  cp_commit();
+  if (nch > 1) issue_chunk(a, wsm + sb, CW, wbase, C, min(C, wlen - C), lane, sval, true);
+  cp_commit();
+  for (int c = 0; c < nch; ++c) {
+    cp_wait_1();
+    __syncwarp();
+    const uint32_t* sw = (const uint32_t*)(wsm + (c & 1) * sb);
+    const T* sv = (const T*)(sw + (1 + a.nother) * CW);
+    const int32_t* sp = (const int32_t*)((const char*)sv + (sval ? (size_t)CW * sizeof(T) : 0));
+    const int ns = min(C, wlen - c * C);
+#pragma unroll 1
+    for (int j = 0; j < ns; ++j) {
+      if (c * C + j >= len) break;
+      const int sj = j * 32 + lane;
+      const uint32_t code = sw[sj];
+      if (code != cur) {
+        const T* src = a.dZ + (int64_t)(code & TK_ROW_MASK) * a.Khat + colbase;
 #pragma unroll
-      for (int jj = 0; jj < MB; ++jj)
+        for (int jj = 0; jj < MB; ++jj)
+#pragma unroll
+          for (int i = 0; i < MA; ++i)
+            D[i + MA * jj] = ((EB || jj < tb) && (EA || i < ka)) ? __ldg(src + i + a.KA * jj) : T(0);
+        cur = code;
+      }
+      const int32_t e = sp[sj];
+      const T w = sval ? sv[sj] : a.vals_override[e];
+      T fq[TK_MAXN - 3];
+      T so = T(1);
+      for (int q = 2; q < a.nother; ++q) {
+        fq[q - 2] = __ldg(a.F[q] + (int64_t)(int32_t)sw[(1 + q) * CW + sj] * a.ld[q] + oc[q - 2]);
+        so *= fq[q - 2];
+      }
+      const int ia = (int32_t)sw[CW + sj];
+      T fa[Row<T, MA>::R];
+      load_row<T, MA>(a.F[0] + (int64_t)ia * a.ld[0], ka, fa);
+      T fb[Row<T, MB>::R];
+      int ib = 0;
+      if (a.nother >= 2) {
+        ib = (int32_t)sw[2 * CW + sj];
+        load_row<T, MB>(a.F[1] + (int64_t)ib * a.ld[1] + j0, tb, fb);
+      } else {
+#pragma unroll
+        for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
+      }
+      T x[MA], y[MB];
+#pragma unroll
+      for (int i = 0; i < MA; ++i) x[i] = T(0);
+#pragma unroll
+      for (int jj = 0; jj < MB; ++jj) {
+        T yy = T(0);
+#pragma unroll
+        for (int i = 0; i < MA; ++i) {
+          x[i] = fma(D[i + MA * jj], fb[jj], x[i]);
+          yy = fma(D[i + MA * jj], fa[i], yy);
+        }
+        y[jj] = yy;
+      }
+      T dot = T(0);
+#pragma unroll
+      for (int i = 0; i < MA; ++i) dot = fma(fa[i], x[i], dot);
+      if (a.dval) {
+        if (a.G == 1) a.dval[e] = so * dot;
+        else atomicAdd(a.dval + e, so * dot);
+      }
+      const T ws = w * so;
+      if (a.dF[0]) {
+        T* d = a.dF[0] + (int64_t)ia * a.ldd[0];
 #pragma unroll
         for (int i = 0; i < MA; ++i)
-          D[i + MA * jj] = ((EB || jj < tb) && (EA || i < ka)) ? __ldg(src + i + a.KA * jj) : T(0);
-      cur = code;
-    }
-    const int32_t e = a.perm[pos];
-    const T w = a.vals_override ? a.vals_override[e] : a.val[pos];
-    T fq[TK_MAXN - 3];
-    T so = T(1);
-    for (int q = 2; q < a.nother; ++q) {
-      fq[q - 2] = __ldg(a.F[q] + (int64_t)a.oidx[q][pos] * a.ld[q] + oc[q - 2]);
-      so *= fq[q - 2];
-    }
-    const int ia = a.oidx[0][pos];
-    T fa[Row<T, MA>::R];
-    load_row<T, MA>(a.F[0] + (int64_t)ia * a.ld[0], ka, fa);
-    T fb[Row<T, MB>::R];
-    int ib = 0;
-    if (a.nother >= 2) {
-      ib = a.oidx[1][pos];
-      load_row<T, MB>(a.F[1] + (int64_t)ib * a.ld[1] + j0, tb, fb);
-    } else {
-#pragma unroll
-      for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
-    }
-    T x[MA], y[MB];
-#pragma unroll
-    for (int i = 0; i < MA; ++i) x[i] = T(0);
-#pragma unroll
-    for (int jj = 0; jj < MB; ++jj) {
-      T yy = T(0);
-#pragma unroll
-      for (int i = 0; i < MA; ++i) {
-        x[i] = fma(D[i + MA * jj], fb[jj], x[i]);
-        yy = fma(D[i + MA * jj], fa[i], yy);
+          if (EA || i < ka) atomicAdd(d + i, ws * x[i]);
       }
-      y[jj] = yy;
-    }
-    T dot = T(0);
+      if (a.nother >= 2 && a.dF[1]) {
+        T* d = a.dF[1] + (int64_t)ib * a.ldd[1] + j0;
 #pragma unroll
-    for (int i = 0; i < MA; ++i) dot = fma(fa[i], x[i], dot);
-    if (a.dval) {
-      if (a.G == 1) a.dval[e] = so * dot;
-      else atomicAdd(a.dval + e, so * dot);
+        for (int jj = 0; jj < MB; ++jj)
+          if (EB || jj < tb) atomicAdd(d + jj, ws * y[jj]);
+      }
+      for (int q = 2; q < a.nother; ++q) {
+        if (!a.dF[q]) continue;
+        T prod = w * dot;
+        for (int q2 = 2; q2 < a.nother; ++q2)
+          if (q2 != q) prod *= fq[q2 - 2];
+        atomicAdd(a.dF[q] + (int64_t)(int32_t)sw[(1 + q) * CW + sj] * a.ldd[q] + oc[q - 2], prod);
+      }
     }
-    const T ws = w * so;
-    if (a.dF[0]) {
-      T* d = a.dF[0] + (int64_t)ia * a.ldd[0];
-#pragma unroll
-      for (int i = 0; i < MA; ++i)
-        if (EA || i < ka) atomicAdd(d + i, ws * x[i]);
-    }
-    if (a.nother >= 2 && a.dF[1]) {
-      T* d = a.dF[1] + (int64_t)ib * a.ldd[1] + j0;
-#pragma unroll
-      for (int jj = 0; jj < MB; ++jj)
-        if (EB || jj < tb) atomicAdd(d + jj, ws * y[jj]);
-    }
-    for (int q = 2; q < a.nother; ++q) {
-      if (!a.dF[q]) continue;
-      T prod = w * dot;
-      for (int q2 = 2; q2 < a.nother; ++q2)
-        if (q2 != q) prod *= fq[q2 - 2];
-      atomicAdd(a.dF[q] + (int64_t)a.oidx[q][pos] * a.ldd[q] + oc[q - 2], prod);
-    }
+    __syncwarp();
+    if (c + 2 < nch) issue_chunk(a, wsm + (c & 1) * sb, CW, wbase, (c + 2) * C, min(C, wlen - (c + 2) * C), lane, sval, true);
+    cp_commit();
   }
+  cp_wait_0();
 }
 
 // Split-slice fix-up, level 1: one CTA per (chunk of <= 256 bins of one split
@@ -446,6 +543,18 @@ TtmcArgs<T> make_args(tucker_ctx* c, int n, const Plan& pl, void* const* F, cons
   return a;
 }
 
+// Staged steps per buffer: 16 for 3-mode FP32, 8 otherwise (keeps a CTA of
+// 4 warps, double-buffered, within 64 KB of shared memory).
+template <typename T>
+int stage_chunk(int nother) {
+  return (sizeof(T) == 4 && nother <= 2) ? 16 : 8;
+}
+
+template <typename K>
+void set_smem_attr(K kernel, int bytes) {
+  TK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(bytes, 48 * 1024)));
+}
+
 unsigned blocks_for(const tk_mode& md, int G) {
   const int64_t warps = (int64_t)(md.Pa / 32) * G;
   return (unsigned)tk_ceil_div(warps, 4);
@@ -461,8 +570,11 @@ void forward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const vo
   a.Zpart = (T*)c->Zpart;
   a.store_vec = ((uintptr_t)Z % 16 == 0) && (md.Khat % VecT<T>::W == 0) &&
                 ((pl.KA * pl.tile.MB) % VecT<T>::W == 0);
+  a.chunk = stage_chunk<T>(pl.nother);
+  const int shm = 4 * 2 * stage_bytes<T>(a.chunk, pl.nother, vals_override == nullptr, vals_override != nullptr);
+  set_smem_attr(fwd_kernel<T>(pl.tile_id), shm);
   tk_phase_begin(c, PH_TTM, s);
-  fwd_kernel<T>(pl.tile_id)<<<blocks_for(md, pl.G), 128, 0, s>>>(a);
+  fwd_kernel<T>(pl.tile_id)<<<blocks_for(md, pl.G), 128, shm, s>>>(a);
   TK_CUDA(cudaGetLastError());
   tk_phase_end(c, s);
   tk_launched(c, PH_TTM);
@@ -494,7 +606,10 @@ void backward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const v
   a.dval = (T*)dval;
   tk_phase_begin(c, PH_BWD, s);
   if (dval && pl.G > 1) TK_CUDA(cudaMemsetAsync(dval, 0, (size_t)c->nnz * sizeof(T), s));
-  bwd_kernel<T>(pl.tile_id)<<<blocks_for(md, pl.G), 128, 0, s>>>(a);
+  a.chunk = stage_chunk<T>(pl.nother);
+  const int shm = 4 * 2 * stage_bytes<T>(a.chunk, pl.nother, vals_override == nullptr, true);
+  set_smem_attr(bwd_kernel<T>(pl.tile_id), shm);
+  bwd_kernel<T>(pl.tile_id)<<<blocks_for(md, pl.G), 128, shm, s>>>(a);
   TK_CUDA(cudaGetLastError());
   tk_phase_end(c, s);
   tk_launched(c, PH_BWD);
@@ -507,8 +622,15 @@ int tk_ttmc_groups(const tucker_ctx* c, int n) { return make_plan(c, n).G; }
 int tk_ttmc_threads_per_sm(const tucker_ctx* c, int n) {
   const Plan pl = make_plan(c, n);
   int nb = 0;
-  if (c->prec == TUCKER_FP32) TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_kernel<float>(pl.tile_id), 128, 0));
-  else TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_kernel<double>(pl.tile_id), 128, 0));
+  if (c->prec == TUCKER_FP32) {
+    const int shm = 4 * 2 * stage_bytes<float>(stage_chunk<float>(pl.nother), pl.nother, true, false);
+    set_smem_attr(fwd_kernel<float>(pl.tile_id), shm);
+    TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_kernel<float>(pl.tile_id), 128, shm));
+  } else {
+    const int shm = 4 * 2 * stage_bytes<double>(stage_chunk<double>(pl.nother), pl.nother, true, false);
+    set_smem_attr(fwd_kernel<double>(pl.tile_id), shm);
+    TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_kernel<double>(pl.tile_id), 128, shm));
+  }
   return std::max(1, nb) * 128;
 }
 
