@@ -115,6 +115,25 @@ tucker_status tucker_stats(tucker_t t, int mode, int64_t* E_max, int64_t* R_sum,
 tucker_status tucker_partition(tucker_t t, int mode, int64_t* d_bin_ptr, int32_t* d_perm, void* stream);
 
 /*
+ * tucker_partition_noalloc -- the same export as tucker_partition, for callers
+ * that cannot allocate device memory while they run (their device memory is
+ * all handed out by their own pool or caching allocator, or a device-wide
+ * synchronising cudaMalloc/cudaFree is not acceptable where they call from).
+ * The paper has no counterpart; it is a deployment convenience.
+ *   - Allocates nothing: the only scratch (the prefix-scan block sums over the
+ *     bin lengths) is a static 256 KiB device array that every GPU loading the
+ *     library holds until exit; bins are limited accordingly (about 16 million
+ *     per mode), larger partitions return TUCKER_ERR_ARG.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - Every call shares the array: calls that overlap on the GPU (other
+ *     streams, other threads) race and must be serialised by the caller.
+ *   - Asynchronous on `stream` (tucker_partition synchronises).
+ */
+tucker_status tucker_partition_noalloc(tucker_t t, int mode, int64_t* d_bin_ptr, int32_t* d_perm, void* stream);
+
+/*
  * ttm_chain -- penultimate matrix Z_(n) = T x_{m != n} F_m^T (Fig. 1
  * "TTM-Chain") through the Kronecker reformulation of Section 3, eq. (1):
  * Z_(n)[l,:] = sum_{e in Slice_n^l} val(e) Kron_n(e), Kron_n as in Appendix A.

@@ -88,6 +88,11 @@ void check_mode(tucker_t t, int mode) {
 }  // namespace
 
 // ------------------------------------------------------------ shared helpers
+// Runs body(arg) with the C-ABI error handling (status code + last-error text).
+tucker_status tk_guarded_call(tucker_ctx* c, void (*body)(void*), void* arg) {
+  return guarded(c, [&] { body(arg); });
+}
+
 void tk_throw(tucker_status code, const std::string& msg) { throw tk_exception{code, msg}; }
 
 void tk_check_cuda(cudaError_t e, const char* what) {

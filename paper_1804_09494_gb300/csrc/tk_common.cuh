@@ -145,6 +145,9 @@ void tk_radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_alt, int3
 void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const void* d_val, int P,
                        cudaStream_t s);
 void tk_partition_export(tucker_ctx* c, int n, int64_t* d_bin_ptr, int32_t* d_perm, cudaStream_t s);
+void tk_partition_export_into(tucker_ctx* c, int n, int64_t* d_bin_ptr, int32_t* d_perm, void* scan_tmp,
+                              cudaStream_t s);
+tucker_status tk_guarded_call(tucker_ctx* c, void (*body)(void*), void* arg);
 
 // ---- TTM-chain (tk_ttmc.cu) ----
 int tk_ttmc_groups(const tucker_ctx* c, int n);

@@ -460,3 +460,15 @@ void tk_partition_export(tucker_ctx* c, int n, int64_t* d_bin_ptr, int32_t* d_pe
   TK_CUDA(cudaGetLastError());
   TK_CUDA(cudaStreamSynchronize(s));
 }
+
+// Same export as tk_partition_export, with the scan's temporary supplied by
+// the caller (at least tk_scan_tmp_bytes(P + 1, 8) bytes) and no host sync.
+void tk_partition_export_into(tucker_ctx* c, int n, int64_t* d_bin_ptr, int32_t* d_perm, void* scan_tmp,
+                              cudaStream_t s) {
+  tk_mode& md = c->mode[n];
+  k_i32_to_i64<<<grid_for(md.P + 1), 256, 0, s>>>(md.bin_len, d_bin_ptr, md.P);
+  TK_CUDA(cudaGetLastError());
+  tk_exclusive_scan_i64(d_bin_ptr, d_bin_ptr, md.P + 1, scan_tmp, s);
+  k_export<<<grid_for(md.cap), 256, 0, s>>>(md.perm, md.bin_len, d_bin_ptr, md.P, md.Pa, md.limit, d_perm);
+  TK_CUDA(cudaGetLastError());
+}

@@ -43,6 +43,7 @@ SIGNATURES = {
     "tucker_last_error": (ctypes.c_char_p, [_VP]),
     "tucker_stats": (ctypes.c_int, [_VP, ctypes.c_int, _P64, _P64, _P64, _P64, _P64]),
     "tucker_partition": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
+    "tucker_partition_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "ttm_chain": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP), _VP, _VP, _VP, _VP]),
     "factor_update": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP, _VP]),
     "core": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), _VP, _VP]),
@@ -186,6 +187,13 @@ class Tucker:
         bin_ptr = torch.empty(P + 1, dtype=torch.int64, device="cuda")
         perm = torch.empty(self.nnz, dtype=torch.int32, device="cuda")
         self._check(self.lib.tucker_partition(self.h, mode, _ptr(bin_ptr), _ptr(perm), _stream()))
+        return bin_ptr, perm
+
+    def partition_noalloc(self, mode, bin_ptr, perm):
+        """tucker_partition_noalloc into caller-owned outputs (P+1 int64, nnz int32)."""
+        _need_cuda(bin_ptr, torch.int64, "bin_ptr")
+        _need_cuda(perm, torch.int32, "perm")
+        self._check(self.lib.tucker_partition_noalloc(self.h, mode, _ptr(bin_ptr), _ptr(perm), _stream()))
         return bin_ptr, perm
 
     def ttm_chain(self, mode, F, vals=None, out=None, row_id=True):
