@@ -251,6 +251,8 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     c->eigA = tk_alloc(c, (size_t)c->maxKhat * c->maxKhat * esz);
     c->eigV = tk_alloc(c, (size_t)c->maxKhat * c->maxKhat * esz);
     c->eigX = (double*)tk_alloc(c, (size_t)2 * c->maxKhat * c->Kmax * 8);
+    c->eigAB = (double*)tk_alloc(c, (size_t)2 * c->maxKhat * 8);
+    c->eigTri = tk_alloc(c, (size_t)6 * c->Kmax * c->maxKhat * esz);
     c->Vs = tk_alloc(c, (size_t)c->maxKhat * c->Kmax * esz);
     c->V = (double*)tk_alloc(c, (size_t)c->maxKhat * c->Kmax * 8);
     c->sigma = (double*)tk_alloc(c, (size_t)TK_MAXK * 8);

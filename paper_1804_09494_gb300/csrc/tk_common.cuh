@@ -98,6 +98,8 @@ struct tucker_ctx {
   int2* gram_tiles = nullptr; // upper-triangle tile list
   int gram_tiles_cap = 0;
   double* eigX = nullptr;   // 2 x Khat x Kmax (eigensolver scratch)
+  double* eigAB = nullptr;  // 2 x Khat (Lanczos tridiagonal)
+  void* eigTri = nullptr;   // Kmax x 6 x Khat (T): tridiagonal LU + inverse-iteration vectors
   void* Vs = nullptr;       // Khat x Kmax (T): V Sigma^-1
   double* V = nullptr;      // Khat x Kmax (eigenvectors)
   double* sigma = nullptr;  // Kmax

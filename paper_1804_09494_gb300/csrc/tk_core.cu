@@ -7,17 +7,22 @@
 
 namespace {
 
+// Deterministic block sum: fixed shuffle tree per warp, warp 0 adds the warp
+// sums in order (FP64 work stays on one warp; red needs 33 slots).
 __device__ double block_sum_fixed(double v, double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
   if (lane == 0) red[w] = v;
   __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];
+  if (w == 0) {
+    double s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) red[32] = s;
+  }
   __syncthreads();
-  return s;
+  return red[32];
 }
 
 // Gpart[split][k][c] = sum over the split's rows r of F[row_id[r]][k] * Z[r][c].
@@ -69,7 +74,7 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_core_final(const double* __restrict__ Gpart, int nsplit, FoldInfo fi,
                                                      double normT2, double* __restrict__ Gd, T* __restrict__ Gout,
                                                      double* __restrict__ fit_out) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   int stride[TK_MAXN];
   {
     int s = 1;
@@ -104,7 +109,7 @@ __global__ void __launch_bounds__(1024) k_core_final(const double* __restrict__ 
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_norm2_partial(const T* __restrict__ v, int64_t n, double* part, int* err) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   double s = 0.0;
   bool bad = false;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(256) k_norm2_partial(const T* __restrict__ v, 
 }
 
 __global__ void k_sum_final(const double* part, int n, double* out) {
-  __shared__ double red[32];
+  __shared__ double red[33];
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) s += part[i];
   s = block_sum_fixed(s, red);

@@ -13,20 +13,6 @@
 
 namespace {
 
-// ------------------------------------------------------------------ block sums
-__device__ double block_sum_d(double v, double* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];  // every thread, same order
-  __syncthreads();
-  return s;
-}
-
 // ------------------------------------------------------------------ Gram
 // Thread (tx, ty) of a 16 x 16 grid owns rows ty + 16 i and columns tx + 16 j of
 // a TM x TM output tile, so shared-memory reads are conflict free.
@@ -41,11 +27,12 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ Z, int R, in
   const int ti = tiles[t].x, tj = tiles[t].y;
   const int r0 = sp * rows_per_split, r1 = min(R, r0 + rows_per_split);
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[RT][RT];
+  // batch sums (acc) are folded into a compensated (Kahan) running sum (tot, cmp)
+  T acc[RT][RT], tot[RT][RT], cmp[RT][RT];
 #pragma unroll
   for (int i = 0; i < RT; ++i)
 #pragma unroll
-    for (int j = 0; j < RT; ++j) acc[i][j] = T(0);
+    for (int j = 0; j < RT; ++j) acc[i][j] = tot[i][j] = cmp[i][j] = T(0);
   for (int rb = r0; rb < r1; rb += BR) {
     for (int i = threadIdx.x; i < BR * TM; i += 256) {
       const int r = i / TM, cc = i - r * TM;
@@ -68,12 +55,22 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ Z, int R, in
         for (int j = 0; j < RT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+      for (int j = 0; j < RT; ++j) {
+        const T y = acc[i][j] - cmp[i][j];
+        const T t2 = tot[i][j] + y;
+        cmp[i][j] = (t2 - tot[i][j]) - y;
+        tot[i][j] = t2;
+        acc[i][j] = T(0);
+      }
   }
   T* out = Wpart + ((int64_t)sp * ntiles + t) * TM * TM;
 #pragma unroll
   for (int i = 0; i < RT; ++i)
 #pragma unroll
-    for (int j = 0; j < RT; ++j) out[(ty + 16 * i) * TM + tx + 16 * j] = acc[i][j];
+    for (int j = 0; j < RT; ++j) out[(ty + 16 * i) * TM + tx + 16 * j] = tot[i][j];
 }
 
 template <typename T>
@@ -94,301 +91,463 @@ __global__ void k_gram_reduce(const T* __restrict__ Wpart, int nsplit, int ntile
   }
 }
 
-// ------------------------------------------------------------------ Jacobi
-template <typename T>
-struct JacobiWork {
-  T* cs;
-  T* sn;
-  int* pp;
-  int* qq;
-};
-
-// Cyclic Jacobi by rounds: the round-robin ("circle") ordering pairs every
-// index with every other once per sweep, n/2 disjoint rotations per round.
-template <typename T>
-__device__ void jacobi_block(T* A, T* V, int n, int max_sweeps, double tol, JacobiWork<T> wk, double* red) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int np = n + (n & 1), half = np / 2;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    double off = 0.0, tot = 0.0;
-    for (int idx = tid; idx < n * n; idx += nt) {
-      const double v = (double)A[idx] * (double)A[idx];
-      tot += v;
-      if (idx / n != idx % n) off += v;
-    }
-    off = block_sum_d(off, red);
-    tot = block_sum_d(tot, red);
-    if (off <= tol * tol * tot) break;
-    for (int r = 0; r < np - 1; ++r) {
-      for (int k = tid; k < half; k += nt) {
-        int p = k == 0 ? 0 : ((k - 1 + r) % (np - 1)) + 1;
-        int q = ((np - 2 - k + r) % (np - 1)) + 1;
-        if (p > q) {
-          const int x = p; p = q; q = x;
-        }
-        T c = T(1), s = T(0);
-        if (q < n) {
-          const T apq = A[p * n + q];
-          if (apq != T(0)) {
-            const T app = A[p * n + p], aqq = A[q * n + q];
-            const T tau = (aqq - app) / (T(2) * apq);
-            const T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-            c = T(1) / sqrt(T(1) + tt * tt);
-            s = tt * c;
-          }
-        }
-        wk.cs[k] = c;
-        wk.sn[k] = s;
-        wk.pp[k] = p;
-        wk.qq[k] = q < n ? q : p;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < half * n; idx += nt) {
-        const int k = idx / n, j = idx - k * n;
-        const T s = wk.sn[k];
-        if (s == T(0)) continue;
-        const T c = wk.cs[k];
-        const int p = wk.pp[k], q = wk.qq[k];
-        const T ap = A[p * n + j], aq = A[q * n + j];
-        A[p * n + j] = c * ap - s * aq;
-        A[q * n + j] = s * ap + c * aq;
-      }
-      __syncthreads();
-      for (int idx = tid; idx < n * half; idx += nt) {
-        const int i = idx / half, k = idx - i * half;
-        const T s = wk.sn[k];
-        if (s == T(0)) continue;
-        const T c = wk.cs[k];
-        const int p = wk.pp[k], q = wk.qq[k];
-        const T ap = A[i * n + p], aq = A[i * n + q];
-        A[i * n + p] = c * ap - s * aq;
-        A[i * n + q] = s * ap + c * aq;
-        const T vp = V[i * n + p], vq = V[i * n + q];
-        V[i * n + p] = c * vp - s * vq;
-        V[i * n + q] = s * vp + c * vq;
-      }
-      __syncthreads();
-    }
-  }
-}
-
-// Index of the largest diagonal entry not yet taken (lowest index on a tie).
-template <typename T>
-__device__ int block_argmax_diag(const T* A, int n, const unsigned char* taken, double* redv, int* redi) {
-  double best = -INFINITY;
-  int bi = n;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    if (taken[i]) continue;
-    const double v = (double)A[i * n + i];
-    if (v > best || (v == best && i < bi)) {
-      best = v;
-      bi = i;
-    }
-  }
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double ov = __shfl_down_sync(0xffffffffu, best, o);
-    const int oi = __shfl_down_sync(0xffffffffu, bi, o);
-    if (ov > best || (ov == best && oi < bi)) {
-      best = ov;
-      bi = oi;
-    }
-  }
-  __syncthreads();
-  if (lane == 0) {
-    redv[w] = best;
-    redi[w] = bi;
-  }
-  __syncthreads();
-  double b = -INFINITY;
-  int r = n;
-  for (int i = 0; i < nw; ++i)
-    if (redv[i] > b || (redv[i] == b && redi[i] < r)) {
-      b = redv[i];
-      r = redi[i];
-    }
-  __syncthreads();
-  return r;
-}
-
 template <typename T>
 struct EigArgs {
   const double* W;
   int n, K;
-  T* gA;
-  T* gV;
+  T* gA;         // n x n (global) when A is not kept in shared memory
+  T* gQ;         // n x n Lanczos basis (global) when not in shared memory
   int use_smem;
   int polish;
-  int max_sweeps;
-  double tol;
-  double* X;     // n x K scratch
-  double* Y;     // n x K scratch
+  double* X;     // n x K scratch (FP64)
+  double* Y;     // n x K scratch (FP64)
+  double* ab;    // 2n: Lanczos alpha, beta
+  T* tri;        // K x 6n: pivoted LU of T - lambda I and the inverse-iteration vector
   double* Vout;  // n x K
   double* sigma; // K
-  T* Vs;         // n x K: Vout[:,k] / sigma_k in T
+  T* Vs;         // n x K: Vout[:,k] / sigma_k
   int* err;
+  unsigned long long* clk;  // optional: clock64() at phase boundaries (profiling; NULL in normal use)
 };
 
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+// deterministic pseudo-random entries in [-0.5, 0.5) for start vectors
+template <typename T>
+__device__ __forceinline__ T hash_unit(uint32_t seed, uint32_t i) {
+  return (T)(int)(mix32(seed * 0x9E3779B9u + i * 0x85EBCA6Bu + 0x165667B1u) >> 8) * (T)(1.0 / 16777216.0) - (T)0.5;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum (blockDim multiple of 32): warp sums, then warp 0 adds the 32
+// partials; red needs 33 slots.  Two barriers; the same value for all threads.
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_allsum(v);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    T s = lane < nw ? red[lane] : T(0);
+    s = warp_allsum(s);
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+// h[k] = q_k . w for k <= j (warp per k); then w -= sum_k h[k] q_k with 8
+// threads per row, each over a stride-8 subset of k, combined by shuffles.
+template <typename T>
+__device__ void reorth_pass(const T* Q, int n, int j, T* w, T* h) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int k = wid; k <= j; k += nw) {
+    const T* q = Q + (size_t)k * n;
+    T d = T(0);
+    for (int i = lane; i < n; i += 32) d = fma(q[i], w[i], d);
+    d = warp_allsum(d);
+    if (lane == 0) h[k] = d;
+  }
+  __syncthreads();
+  const int part = threadIdx.x & 7;
+  const int rows_per_pass = blockDim.x >> 3;
+  for (int i0 = 0; i0 < n; i0 += rows_per_pass) {
+    const int i = i0 + (threadIdx.x >> 3);
+    T acc = T(0);
+    if (i < n)
+      for (int k = part; k <= j; k += 8) acc = fma(h[k], Q[(size_t)k * n + i], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    if (i < n && part == 0) w[i] -= acc;
+  }
+  __syncthreads();
+}
+
+// number of eigenvalues of the symmetric tridiagonal (a, b2 = off-diagonal^2) below x
+template <typename T>
+__device__ int sturm_count(const T* a, const T* b2, int m, T x, T pivmin) {
+  int cnt = 0;
+  T d = a[0] - x;
+  if (fabs(d) < pivmin) d = -pivmin;
+  cnt += d < T(0);
+  for (int i = 1; i < m; ++i) {
+    d = (a[i] - x) - b2[i - 1] / d;
+    if (fabs(d) < pivmin) d = -pivmin;
+    cnt += d < T(0);
+  }
+  return cnt;
+}
+
+// One thread: factor T - lam I (symmetric tridiagonal: diagonal a, off-diagonal
+// b) by Gaussian elimination with partial pivoting; the upper factor has two
+// superdiagonals.  `lu` holds 5m values.
+template <typename T>
+__device__ void tri_factor(const T* a, const T* b, int m, T lam, T tiny, T* lu) {
+  T* u0 = lu;
+  T* u1 = lu + m;
+  T* u2 = lu + 2 * m;
+  T* l = lu + 3 * m;
+  T* pv = lu + 4 * m;
+  T p = a[0] - lam, q = m > 1 ? b[0] : T(0), r = T(0);
+  for (int i = 0; i < m - 1; ++i) {
+    const T s = b[i], t = a[i + 1] - lam, u = (i + 2 < m) ? b[i + 1] : T(0);
+    if (fabs(p) >= fabs(s)) {
+      const T piv = (p == T(0)) ? tiny : p;
+      u0[i] = piv;
+      u1[i] = q;
+      u2[i] = r;
+      const T mult = s / piv;
+      l[i] = mult;
+      pv[i] = T(0);
+      p = t - mult * q;
+      q = u - mult * r;
+      r = T(0);
+    } else {
+      u0[i] = s;
+      u1[i] = t;
+      u2[i] = u;
+      const T mult = p / s;
+      l[i] = mult;
+      pv[i] = T(1);
+      p = q - mult * t;
+      q = r - mult * u;
+      r = T(0);
+    }
+  }
+  u0[m - 1] = (fabs(p) < tiny) ? (p < T(0) ? -tiny : tiny) : p;
+  u1[m - 1] = T(0);
+  u2[m - 1] = T(0);
+}
+
+// Solves with the factor of tri_factor; x holds the right-hand side on entry.
+template <typename T>
+__device__ void tri_solve(const T* lu, int m, T* x) {
+  const T* u0 = lu;
+  const T* u1 = lu + m;
+  const T* u2 = lu + 2 * m;
+  const T* l = lu + 3 * m;
+  const T* pv = lu + 4 * m;
+  T top = x[0];
+  for (int i = 0; i < m - 1; ++i) {
+    const T bot = x[i + 1];
+    if (pv[i] == T(0)) {
+      x[i] = top;
+      top = bot - l[i] * top;
+    } else {
+      x[i] = bot;
+      top = top - l[i] * bot;
+    }
+  }
+  x[m - 1] = top;
+  for (int i = m - 1; i >= 0; --i) {
+    T v = x[i];
+    if (i + 1 < m) v -= u1[i] * x[i + 1];
+    if (i + 2 < m) v -= u2[i] * x[i + 2];
+    x[i] = v / u0[i];
+  }
+}
+
+// Top-K eigenpairs of the symmetric n x n Gram matrix W in one CTA, in the
+// context precision T:
+//   Lanczos tridiagonalisation T = Q^T W Q with full re-orthogonalisation
+//   (classical Gram-Schmidt, twice); multisection (parallel Sturm counts) for
+//   the K largest eigenvalues of T; inverse iteration (pivoted tridiagonal LU)
+//   for their eigenvectors; back-transformation X = Q S and modified
+//   Gram-Schmidt.  With `polish` (FP32 context) the basis is refined in FP64:
+//   Y = W X, then CholeskyQR of Y gives the basis X' = Y R^-1 and R_kk ~ lambda_k.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double red[32];
-  __shared__ int redi[32];
-  __shared__ double H[TK_MAXK * TK_MAXK];
-  __shared__ double HV[TK_MAXK * TK_MAXK];
-  __shared__ double hcs[TK_MAXK / 2 + 1], hsn[TK_MAXK / 2 + 1];
-  __shared__ int hpp[TK_MAXK / 2 + 1], hqq[TK_MAXK / 2 + 1];
-  __shared__ int sel[TK_MAXK];
-  __shared__ unsigned char taken[TK_MAXKHAT];
+  __shared__ T red[33];
+  __shared__ double redd[33];
+  __shared__ double lo_s[TK_MAXK], hi_s[TK_MAXK];
+  __shared__ T lam_s[TK_MAXK], inv_sig[TK_MAXK];
+  __shared__ double C[TK_MAXK][TK_MAXK + 1];
+  __shared__ double Ri[TK_MAXK][TK_MAXK + 1];
+  __shared__ int cnt_s[1024];
+  __shared__ T mn_s[32], mx_s[32], b2_s[32];
   const int n = a.n, K = a.K, tid = threadIdx.x, nt = blockDim.x;
-  const int half = (n + 1) / 2;
+  const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
+  const int m = n;
   unsigned char* p = smem;
   T* A;
-  T* V;
+  T* Q;
   if (a.use_smem) {
     A = (T*)p;
     p += (size_t)n * n * sizeof(T);
-    V = (T*)p;
-    p += (size_t)n * n * sizeof(T);
+    Q = (T*)p;
+    p += (size_t)n * m * sizeof(T);
   } else {
     A = a.gA;
-    V = a.gV;
+    Q = a.gQ;
   }
-  JacobiWork<T> wk;
-  wk.cs = (T*)p;
-  p += (size_t)half * sizeof(T);
-  wk.sn = (T*)p;
-  p += (size_t)half * sizeof(T);
-  wk.pp = (int*)p;
-  p += (size_t)half * sizeof(int);
-  wk.qq = (int*)p;
+  T* w = (T*)p;
+  p += (size_t)n * sizeof(T);
+  T* h = (T*)p;
+  p += (size_t)m * sizeof(T);
+  T* ta = (T*)p;
+  p += (size_t)m * sizeof(T);
+  T* tb = (T*)p;
+  p += (size_t)m * sizeof(T);
+  T* tb2 = (T*)p;
+
+  T fro2 = T(0);
   for (int idx = tid; idx < n * n; idx += nt) {
-    A[idx] = (T)a.W[idx];
-    V[idx] = (idx / n == idx % n) ? T(1) : T(0);
+    const T v = (T)a.W[idx];
+    A[idx] = v;
+    fro2 = fma(v, v, fro2);
   }
-  for (int i = tid; i < n; i += nt) taken[i] = 0;
-  __syncthreads();
-  jacobi_block<T>(A, V, n, a.max_sweeps, a.tol, wk, red);
-  __syncthreads();
-  for (int kk = 0; kk < K; ++kk) {
-    const int i = block_argmax_diag<T>(A, n, taken, red, redi);
-    if (tid == 0) {
-      sel[kk] = i < n ? i : 0;
-      taken[i < n ? i : 0] = 1;
+  const T fro = sqrt(block_sum<T>(fro2, red));
+  const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16);
+  if (a.clk && tid == 0) a.clk[0] = clock64();
+
+  // ---- Lanczos
+  for (int i = tid; i < n; i += nt) w[i] = hash_unit<T>(1, i);
+  {
+    T nn = T(0);
+    for (int i = tid; i < n; i += nt) nn = fma(w[i], w[i], nn);
+    const T inv = T(1) / sqrt(block_sum<T>(nn, red));
+    for (int i = tid; i < n; i += nt) Q[i] = w[i] * inv;
+    __syncthreads();
+  }
+  for (int j = 0; j < m; ++j) {
+    const T* qj = Q + (size_t)j * n;
+    for (int r = wid; r < n; r += nw) {  // w = A q_j, warp per row
+      const T* ar = A + (size_t)r * n;
+      T sacc = T(0);
+      for (int cidx = lane; cidx < n; cidx += 32) sacc = fma(ar[cidx], qj[cidx], sacc);
+      sacc = warp_allsum(sacc);
+      if (lane == 0) w[r] = sacc;
+    }
+    __syncthreads();
+    reorth_pass<T>(Q, n, j, w, h);
+    T al = h[j];
+    reorth_pass<T>(Q, n, j, w, h);
+    al += h[j];
+    if (tid == 0) ta[j] = al;
+    T nn = T(0);
+    for (int i = tid; i < n; i += nt) nn = fma(w[i], w[i], nn);
+    const T bnorm = sqrt(block_sum<T>(nn, red));
+    if (j == m - 1) break;
+    T* qn = Q + (size_t)(j + 1) * n;
+    if (bnorm > T(100) * eps * fro) {
+      if (tid == 0) tb[j] = bnorm;
+      const T inv = T(1) / bnorm;
+      for (int i = tid; i < n; i += nt) qn[i] = w[i] * inv;
+    } else {
+      // invariant subspace found: restart with a fresh vector orthogonal to q_0..q_j
+      if (tid == 0) tb[j] = T(0);
+      for (int i = tid; i < n; i += nt) w[i] = hash_unit<T>(j + 2, i);
+      __syncthreads();
+      reorth_pass<T>(Q, n, j, w, h);
+      reorth_pass<T>(Q, n, j, w, h);
+      T n2 = T(0);
+      for (int i = tid; i < n; i += nt) n2 = fma(w[i], w[i], n2);
+      n2 = block_sum<T>(n2, red);
+      const T inv = n2 > T(0) ? T(1) / sqrt(n2) : T(0);
+      for (int i = tid; i < n; i += nt) qn[i] = w[i] * inv;
     }
     __syncthreads();
   }
-  // X = selected eigenvectors (FP64)
+  if (tid == 0) tb[m - 1] = T(0);
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[1] = clock64();
+
+  // ---- Gershgorin interval and pivot threshold
+  {
+    T mn = T(INFINITY), mx = T(-INFINITY), b2m = T(0);
+    for (int i = tid; i < m; i += nt) {
+      const T bb = tb[i];
+      tb2[i] = bb * bb;
+      const T r = (i > 0 ? fabs(tb[i - 1]) : T(0)) + fabs(bb);
+      mn = fmin(mn, ta[i] - r);
+      mx = fmax(mx, ta[i] + r);
+      b2m = fmax(b2m, bb * bb);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      b2m = fmax(b2m, __shfl_xor_sync(0xffffffffu, b2m, o));
+    }
+    if (lane == 0) {
+      mn_s[wid] = mn;
+      mx_s[wid] = mx;
+      b2_s[wid] = b2m;
+    }
+    __syncthreads();
+    if (tid < K) {
+      T lo = T(INFINITY), hi = T(-INFINITY);
+      for (int i = 0; i < nw; ++i) {
+        lo = fmin(lo, mn_s[i]);
+        hi = fmax(hi, mx_s[i]);
+      }
+      const T pad = T(1e-6) * (hi - lo) + T(10) * eps * fabs(hi) + T(1e-30);
+      lo_s[tid] = (double)(lo - pad);
+      hi_s[tid] = (double)(hi + pad);
+    }
+    if (tid == 0) {
+      T b2 = T(0);
+      for (int i = 0; i < nw; ++i) b2 = fmax(b2, b2_s[i]);
+      red[0] = (sizeof(T) == 4 ? T(1e-30) : T(1e-290)) * fmax(T(1), b2);
+    }
+    __syncthreads();
+  }
+  const T pivmin = red[0];
+  __syncthreads();
+  // ---- multisection for the K largest eigenvalues of T
+  const int S = nt / K;
+  const double inv_s1 = 1.0 / (double)(S + 1);
+  const int rounds = sizeof(T) == 4 ? 5 : 9;
+  for (int rd = 0; rd < rounds; ++rd) {
+    const int k = tid / S, sidx = tid - k * S;
+    if (k < K) {
+      const double step = (hi_s[k] - lo_s[k]) * inv_s1;
+      cnt_s[tid] = sturm_count<T>(ta, tb2, m, (T)(lo_s[k] + step * (double)(sidx + 1)), pivmin);
+    }
+    __syncthreads();
+    if (tid < K) {
+      const int target = m - 1 - tid;  // ascending index of the (tid+1)-th largest eigenvalue
+      const double l0 = lo_s[tid], step = (hi_s[tid] - l0) * inv_s1;
+      double nlo = l0, nhi = hi_s[tid];
+      for (int s2 = 0; s2 < S; ++s2) {
+        if (cnt_s[tid * S + s2] <= target) {
+          nlo = l0 + step * (double)(s2 + 1);
+        } else {
+          nhi = l0 + step * (double)(s2 + 1);
+          break;
+        }
+      }
+      lo_s[tid] = nlo;
+      hi_s[tid] = nhi;
+    }
+    __syncthreads();
+  }
+  if (tid < K) lam_s[tid] = (T)(0.5 * (lo_s[tid] + hi_s[tid]));
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[2] = clock64();
+  // ---- inverse iteration, one thread per eigenvalue
+  for (int k = tid; k < K; k += nt) {
+    T* lu = a.tri + (size_t)k * 6 * m;
+    T* x = lu + 5 * m;
+    const T tiny = eps * fro + T(1e-30);
+    tri_factor<T>(ta, tb, m, lam_s[k], tiny, lu);
+    for (int i = 0; i < m; ++i) x[i] = hash_unit<T>(101 + k, i);
+    for (int it = 0; it < 3; ++it) {
+      tri_solve<T>(lu, m, x);
+      T nn = T(0);
+      for (int i = 0; i < m; ++i) nn = fma(x[i], x[i], nn);
+      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
+      for (int i = 0; i < m; ++i) x[i] *= inv;
+    }
+  }
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[3] = clock64();
+  // ---- X = Q S, then modified Gram-Schmidt (separates clustered eigenvalues)
   for (int idx = tid; idx < n * K; idx += nt) {
     const int i = idx / K, k = idx - i * K;
-    a.X[idx] = (double)V[i * n + sel[k]];
+    const T* x = a.tri + (size_t)k * 6 * m + 5 * m;
+    T s2 = T(0);
+    for (int j = 0; j < m; ++j) s2 = fma(Q[(size_t)j * n + i], x[j], s2);
+    a.X[idx] = (double)s2;
   }
   __syncthreads();
+  if (a.clk && tid == 0) a.clk[4] = clock64();
+  for (int k = 0; k < K; ++k) {
+    for (int j = 0; j < k; ++j) {
+      T d = T(0);
+      for (int i = tid; i < n; i += nt) d = fma((T)a.X[i * K + j], (T)a.X[i * K + k], d);
+      d = block_sum<T>(d, red);
+      for (int i = tid; i < n; i += nt) a.X[i * K + k] = (double)((T)a.X[i * K + k] - d * (T)a.X[i * K + j]);
+      __syncthreads();
+    }
+    T nn = T(0);
+    for (int i = tid; i < n; i += nt) nn = fma((T)a.X[i * K + k], (T)a.X[i * K + k], nn);
+    nn = block_sum<T>(nn, red);
+    const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
+    for (int i = tid; i < n; i += nt) a.X[i * K + k] = (double)((T)a.X[i * K + k] * inv);
+    __syncthreads();
+  }
+  if (a.clk && tid == 0) a.clk[5] = clock64();
   if (a.polish) {
-    // modified Gram-Schmidt in FP64
-    for (int k = 0; k < K; ++k) {
-      for (int j = 0; j < k; ++j) {
-        double d = 0.0;
-        for (int i = tid; i < n; i += nt) d += a.X[i * K + j] * a.X[i * K + k];
-        d = block_sum_d(d, red);
-        for (int i = tid; i < n; i += nt) a.X[i * K + k] -= d * a.X[i * K + j];
-        __syncthreads();
-      }
-      double nn = 0.0;
-      for (int i = tid; i < n; i += nt) nn += a.X[i * K + k] * a.X[i * K + k];
-      nn = block_sum_d(nn, red);
-      const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-      for (int i = tid; i < n; i += nt) a.X[i * K + k] *= inv;
-      __syncthreads();
-    }
-    // one subspace step Y = W X, then Rayleigh-Ritz on span(Y)
+    // FP64 refinement: Y = W X, C = Y^T Y, C = R^T R, X' = Y R^-1, sigma_k^2 ~ R_kk
     for (int idx = tid; idx < n * K; idx += nt) {
       const int i = idx / K, k = idx - i * K;
-      double s = 0.0;
+      double s2 = 0.0;
       const double* wr = a.W + (int64_t)i * n;
-      for (int cc = 0; cc < n; ++cc) s = fma(wr[cc], a.X[cc * K + k], s);
-      a.Y[idx] = s;
+      for (int cc = 0; cc < n; ++cc) s2 = fma(wr[cc], a.X[cc * K + k], s2);
+      a.Y[idx] = s2;
     }
     __syncthreads();
-    for (int k = 0; k < K; ++k) {  // orthonormalise Y (MGS) -> new basis X
-      for (int j = 0; j < k; ++j) {
-        double d = 0.0;
-        for (int i = tid; i < n; i += nt) d += a.Y[i * K + j] * a.Y[i * K + k];
-        d = block_sum_d(d, red);
-        for (int i = tid; i < n; i += nt) a.Y[i * K + k] -= d * a.Y[i * K + j];
-        __syncthreads();
+    if (a.clk && tid == 0) a.clk[6] = clock64();
+    for (int pr = tid; pr < K * K; pr += nt) {
+      const int r = pr / K, cc = pr - r * K;
+      if (r <= cc) {
+        double s2 = 0.0;
+        for (int i = 0; i < n; ++i) s2 = fma(a.Y[i * K + r], a.Y[i * K + cc], s2);
+        C[r][cc] = s2;
+        C[cc][r] = s2;
       }
-      double nn = 0.0;
-      for (int i = tid; i < n; i += nt) nn += a.Y[i * K + k] * a.Y[i * K + k];
-      nn = block_sum_d(nn, red);
-      const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-      for (int i = tid; i < n; i += nt) {
-        a.Y[i * K + k] *= inv;
-        a.X[i * K + k] = a.Y[i * K + k];
-      }
-      __syncthreads();
     }
-    // Y = W X ; H = X^T Y
+    __syncthreads();
+    if (wid == 0) {  // Cholesky C = L L^T (lower, in place) and Ri = L^-T (upper), one warp
+      bool bad = false;
+      for (int j = 0; j < K; ++j) {
+        double d = C[j][j];
+        if (!(d > 0.0)) bad = true;
+        d = d > 0.0 ? sqrt(d) : 1.0;
+        __syncwarp();
+        if (lane == j) C[j][j] = d;
+        if (lane > j && lane < K) C[lane][j] /= d;
+        __syncwarp();
+        if (lane > j && lane < K)
+          for (int k2 = j + 1; k2 <= lane; ++k2) C[lane][k2] -= C[lane][j] * C[k2][j];
+        __syncwarp();
+      }
+      if (bad && lane == 0) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
+      if (lane < K) {
+        for (int i = K - 1; i >= 0; --i) {
+          double s2 = (i == lane) ? 1.0 : 0.0;
+          for (int k2 = i + 1; k2 < K; ++k2) s2 -= C[k2][i] * Ri[k2][lane];
+          Ri[i][lane] = (i <= lane) ? s2 / C[i][i] : 0.0;
+        }
+        a.sigma[lane] = sqrt(fabs(C[lane][lane]));  // R_kk ~ lambda_k, sigma_k = sqrt(lambda_k)
+      }
+    }
+    __syncthreads();
     for (int idx = tid; idx < n * K; idx += nt) {
       const int i = idx / K, k = idx - i * K;
-      double s = 0.0;
-      const double* wr = a.W + (int64_t)i * n;
-      for (int cc = 0; cc < n; ++cc) s = fma(wr[cc], a.X[cc * K + k], s);
-      a.Y[idx] = s;
+      double s2 = 0.0;
+      for (int j = 0; j <= k; ++j) s2 = fma(a.Y[i * K + j], Ri[j][k], s2);
+      a.Vout[idx] = s2;
     }
-    __syncthreads();
-    for (int idx = tid; idx < K * K; idx += nt) {
-      const int r = idx / K, cidx = idx - r * K;
-      double s = 0.0;
-      for (int i = 0; i < n; ++i) s = fma(a.X[i * K + r], a.Y[i * K + cidx], s);
-      H[idx] = s;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < K * K; idx += nt) {
-      const int r = idx / K, cidx = idx - r * K;
-      HV[idx] = (r == cidx) ? 1.0 : 0.0;
-      if (r < cidx) {
-        const double m = 0.5 * (H[idx] + H[cidx * K + r]);
-        H[idx] = m;
-        H[cidx * K + r] = m;
-      }
-    }
-    __syncthreads();
-    JacobiWork<double> hw{hcs, hsn, hpp, hqq};
-    jacobi_block<double>(H, HV, K, 40, 1e-15, hw, red);
-    for (int i = tid; i < K; i += nt) taken[i] = 0;
-    __syncthreads();
-    for (int kk = 0; kk < K; ++kk) {
-      const int i = block_argmax_diag<double>(H, K, taken, red, redi);
-      if (tid == 0) {
-        sel[kk] = i < K ? i : 0;
-        taken[i < K ? i : 0] = 1;
-      }
-      __syncthreads();
-    }
-    for (int idx = tid; idx < n * K; idx += nt) {
-      const int i = idx / K, k = idx - i * K;
-      double s = 0.0;
-      for (int j = 0; j < K; ++j) s = fma(a.X[i * K + j], HV[j * K + sel[k]], s);
-      a.Vout[idx] = s;
-    }
-    for (int k = tid; k < K; k += nt) a.sigma[k] = sqrt(fmax(H[sel[k] * K + sel[k]], 0.0));
   } else {
     for (int idx = tid; idx < n * K; idx += nt) a.Vout[idx] = a.X[idx];
-    for (int k = tid; k < K; k += nt) a.sigma[k] = sqrt(fmax((double)A[sel[k] * n + sel[k]], 0.0));
+    for (int k = tid; k < K; k += nt) a.sigma[k] = sqrt(fmax((double)lam_s[k], 0.0));
   }
   __syncthreads();
-  for (int idx = tid; idx < n * K; idx += nt) {
-    const int k = idx % K;
-    const double sg = a.sigma[k];
-    if (!(sg > 0.0) || !isfinite(sg)) {
-      if (idx < K) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
-      a.Vs[idx] = T(0);
-    } else {
-      a.Vs[idx] = (T)(a.Vout[idx] / sg);
-    }
+  if (tid < K) {
+    const double sg = a.sigma[tid];
+    const bool ok = sg > 0.0 && isfinite(sg);
+    if (!ok) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
+    inv_sig[tid] = ok ? (T)(1.0 / sg) : T(0);
   }
+  __syncthreads();
+  for (int idx = tid; idx < n * K; idx += nt) a.Vs[idx] = (T)a.Vout[idx] * inv_sig[idx % K];
+  if (a.clk && tid == 0) a.clk[7] = clock64();
 }
 
 // ------------------------------------------------------------------ back-projection
@@ -524,24 +683,28 @@ __global__ void k_chol_inv(const double* __restrict__ Cpart, int nblk, int K, co
   }
 }
 
+template <typename T>
 struct Cand {
-  double a;  // |value|
-  int r;     // compact row (increasing slice id)
-  double v;  // signed value
+  T a;    // |value|
+  int r;  // compact row (increasing slice id)
+  T v;    // signed value
 };
-__device__ __forceinline__ bool better(const Cand& x, const Cand& y) { return x.a > y.a || (x.a == y.a && x.r < y.r); }
+template <typename T>
+__device__ __forceinline__ bool better(const Cand<T>& x, const Cand<T>& y) {
+  return x.a > y.a || (x.a == y.a && x.r < y.r);
+}
 
 // U <- U M (row by row) and per-block best (|value|, lowest row) per column.
 template <typename T>
 __global__ void __launch_bounds__(256) k_apply(T* __restrict__ U, int R, int K, const double* __restrict__ M,
                                                double* __restrict__ colbest) {
   __shared__ T Ms[TK_MAXK][TK_MAXK];
-  __shared__ Cand wbest[8][TK_MAXK];
+  __shared__ Cand<T> wbest[8][TK_MAXK];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   for (int i = tid; i < K * K; i += 256) Ms[i / K][i % K] = (T)M[i];
   __syncthreads();
-  Cand best[TK_MAXK];
-  for (int k = 0; k < K; ++k) best[k] = Cand{-1.0, 0x7fffffff, 0.0};
+  Cand<T> best[TK_MAXK];
+  for (int k = 0; k < K; ++k) best[k] = Cand<T>{T(-1), 0x7fffffff, T(0)};
   for (int r = blockIdx.x * 256 + tid; r < R; r += gridDim.x * 256) {
     T u[TK_MAXK], v[TK_MAXK];
     for (int k = 0; k < K; ++k) u[k] = U[(int64_t)r * K + k];
@@ -552,15 +715,15 @@ __global__ void __launch_bounds__(256) k_apply(T* __restrict__ U, int R, int K, 
     }
     for (int k = 0; k < K; ++k) {
       U[(int64_t)r * K + k] = v[k];
-      const Cand c{fabs((double)v[k]), r, (double)v[k]};
+      const Cand<T> c{fabs(v[k]), r, v[k]};
       if (better(c, best[k])) best[k] = c;
     }
   }
   for (int k = 0; k < K; ++k) {
-    Cand c = best[k];
+    Cand<T> c = best[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      Cand d;
+      Cand<T> d;
       d.a = __shfl_down_sync(0xffffffffu, c.a, o);
       d.r = __shfl_down_sync(0xffffffffu, c.r, o);
       d.v = __shfl_down_sync(0xffffffffu, c.v, o);
@@ -570,23 +733,23 @@ __global__ void __launch_bounds__(256) k_apply(T* __restrict__ U, int R, int K, 
   }
   __syncthreads();
   if (tid < K) {
-    Cand c = wbest[0][tid];
+    Cand<T> c = wbest[0][tid];
     for (int ww = 1; ww < 8; ++ww)
       if (better(wbest[ww][tid], c)) c = wbest[ww][tid];
     double* o = colbest + ((int64_t)blockIdx.x * K + tid) * 3;
-    o[0] = c.a;
+    o[0] = (double)c.a;
     o[1] = (double)c.r;
-    o[2] = c.v;
+    o[2] = (double)c.v;
   }
 }
 
 __global__ void k_signs(const double* colbest, int nblk, int K, double* sign) {
   const int k = threadIdx.x;
   if (k >= K) return;
-  Cand c{-1.0, 0x7fffffff, 0.0};
+  Cand<double> c{-1.0, 0x7fffffff, 0.0};
   for (int b = 0; b < nblk; ++b) {
     const double* o = colbest + ((int64_t)b * K + k) * 3;
-    const Cand d{o[0], (int)o[1], o[2]};
+    const Cand<double> d{o[0], (int)o[1], o[2]};
     if (better(d, c)) c = d;
   }
   sign[k] = c.v < 0.0 ? -1.0 : 1.0;
@@ -634,8 +797,12 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     int2* dtiles = c->gram_tiles;
     TK_CUDA(cudaMemcpyAsync(dtiles, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     dim3 grid(ntiles, nsplit);
-    if (TM == 128) k_gram<T, 128><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
-    else k_gram<T, 64><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
+    if constexpr (sizeof(T) == 4) {
+      if (TM == 128) k_gram<T, 128><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
+      else k_gram<T, 64><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
+    } else {
+      k_gram<T, 64><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
+    }
     TK_CUDA(cudaGetLastError());
     const unsigned g2 = (unsigned)std::min<int64_t>(tk_ceil_div((int64_t)Khat * Khat, 256), 4096);
     k_gram_reduce<T><<<g2, 256, 0, s>>>((const T*)c->Wpart, nsplit, ntiles, tpd, TM, Khat, c->W);
@@ -653,17 +820,16 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     a.n = Khat;
     a.K = K;
     a.gA = (T*)c->eigA;
-    a.gV = (T*)c->eigV;
+    a.gQ = (T*)c->eigV;
     const size_t mat = (size_t)2 * Khat * Khat * sizeof(T);
-    const int half = (Khat + 1) / 2;
-    const size_t work = (size_t)half * (2 * sizeof(T) + 2 * sizeof(int)) + 64;
-    a.use_smem = (mat + work) <= 140 * 1024;
+    const size_t work = (size_t)5 * Khat * sizeof(T) + 64;
+    a.use_smem = (mat + work) <= 150 * 1024;
     const size_t shm = (a.use_smem ? mat : 0) + work;
     a.polish = c->prec == TUCKER_FP32;
-    a.max_sweeps = sizeof(T) == 4 ? 20 : 40;
-    a.tol = sizeof(T) == 4 ? 1e-6 : 1e-13;
     a.X = c->eigX;
     a.Y = c->eigX + (size_t)Khat * K;
+    a.ab = c->eigAB;
+    a.tri = (T*)c->eigTri;
     a.Vout = c->V;
     a.sigma = c->sigma;
     a.Vs = (T*)c->Vs;
