@@ -257,7 +257,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     c->V = (double*)tk_alloc(c, (size_t)c->maxKhat * c->Kmax * 8);
     c->sigma = (double*)tk_alloc(c, (size_t)TK_MAXK * 8);
     c->U = tk_alloc(c, (size_t)c->maxR * c->Kmax * esz);
-    c->Cpart = (double*)tk_alloc(c, (size_t)2 * c->sm_count * TK_MAXK * TK_MAXK * 8);
+    c->Cpart = (double*)tk_alloc(c, (size_t)4 * c->sm_count * TK_MAXK * TK_MAXK * 8);
     c->Rinv = (double*)tk_alloc(c, (size_t)3 * TK_MAXK * TK_MAXK * 8);
     c->colbest = (double*)tk_alloc(c, (size_t)2 * c->sm_count * TK_MAXK * 3 * 8);
     c->Gpart = (double*)tk_alloc(c, gp * 8);

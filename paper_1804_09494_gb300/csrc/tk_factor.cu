@@ -8,6 +8,7 @@
 //   signs                column's entry of largest magnitude (lowest slice id on a tie) made positive
 //   F_n[row_id[r]] = U[r], rows of empty slices zero
 #include <algorithm>
+#include <type_traits>
 
 #include "tk_common.cuh"
 
@@ -73,11 +74,18 @@ __global__ void __launch_bounds__(256) k_gram(const T* __restrict__ Z, int R, in
     for (int j = 0; j < RT; ++j) out[(ty + 16 * i) * TM + tx + 16 * j] = tot[i][j];
 }
 
+// W (FP64, both triangles) from the split partials: 8 lanes per entry, each
+// summing every 8th split in order, combined by a fixed shuffle tree.
 template <typename T>
 __global__ void k_gram_reduce(const T* __restrict__ Wpart, int nsplit, int ntiles, int tpd, int TM, int Khat,
                               double* __restrict__ W) {
   const int64_t total = (int64_t)Khat * Khat;
-  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+  const int part = threadIdx.x & 7;
+  const int64_t per_pass = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  for (int64_t base = 0; base < total; base += per_pass) {  // uniform trip count for every lane
+    const int64_t idx0 = base + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3);
+    const bool live = idx0 < total;
+    const int64_t idx = live ? idx0 : 0;
     int i = (int)(idx / Khat), j = (int)(idx - (int64_t)i * Khat);
     int ti = i / TM, tj = j / TM, ii = i - ti * TM, jj = j - tj * TM;
     if (ti > tj) {
@@ -86,8 +94,12 @@ __global__ void k_gram_reduce(const T* __restrict__ Wpart, int nsplit, int ntile
     }
     const int t = ti * tpd - ti * (ti - 1) / 2 + (tj - ti);
     double s = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) s += (double)Wpart[((int64_t)sp * ntiles + t) * TM * TM + ii * TM + jj];
-    W[idx] = s;
+    if (live)
+      for (int sp = part; sp < nsplit; sp += 8) s += (double)Wpart[((int64_t)sp * ntiles + t) * TM * TM + ii * TM + jj];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (part == 0 && live) W[idx] = s;
   }
 }
 
@@ -572,6 +584,122 @@ __global__ void __launch_bounds__(256) k_backproj(const T* __restrict__ Z, int R
   }
 }
 
+// Tiled back-projection: a tile of 128 rows of Z is copied with coalesced
+// 16-byte loads into shared memory (row stride Khat+1 words, so the per-thread
+// row reads are conflict free), V Sigma^-1 sits in shared memory with rows
+// padded to 16 bytes (vector reads), and each thread forms one row of U = Z Vs.
+// With GRAM the thread also accumulates u u^T (upper triangle) over its rows
+// and each block writes an FP64 partial of U^T U (the first CholeskyQR Gram).
+template <typename T, int KM, bool GRAM>
+__global__ void __launch_bounds__(128) k_backproj_tile(const T* __restrict__ Z, int R, int Khat,
+                                                       const T* __restrict__ Vs, int K, T* __restrict__ U,
+                                                       double* __restrict__ Cpart) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NP = GRAM ? KM * (KM + 1) / 2 : 1;
+  constexpr int W = 16 / sizeof(T);
+  constexpr int KP = (KM + W - 1) / W * W;  // padded row of Vs
+  using V = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+  __shared__ T wsum[4][NP];
+  T* vs = (T*)smraw;             // Khat x KP
+  T* tile = vs + Khat * KP;      // 128 x (Khat + 1)
+  const int ld = Khat + 1;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < Khat * KP; i += 128) {
+    const int cc = i / KP, k = i - cc * KP;
+    vs[i] = k < K ? Vs[cc * K + k] : T(0);
+  }
+  T g[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) g[q] = T(0);
+  for (int r0 = blockIdx.x * 128; r0 < R; r0 += gridDim.x * 128) {
+    __syncthreads();
+    const int nr = min(128, R - r0);
+    const T* src = Z + (int64_t)r0 * Khat;
+    const int total = nr * Khat;
+    if (Khat % W == 0) {
+      const V* s4 = reinterpret_cast<const V*>(src);
+      for (int e = tid; e < total / W; e += 128) {
+        const V x = s4[e];
+        const int f = e * W, r = f / Khat, cc = f - r * Khat;
+        T* d = tile + r * ld + cc;
+        if constexpr (sizeof(T) == 4) {
+          d[0] = x.x; d[1] = x.y; d[2] = x.z; d[3] = x.w;
+        } else {
+          d[0] = x.x; d[1] = x.y;
+        }
+      }
+    } else {
+      for (int e = tid; e < total; e += 128) {
+        const int r = e / Khat, cc = e - r * Khat;
+        tile[r * ld + cc] = src[e];
+      }
+    }
+    __syncthreads();
+    if (tid < nr) {
+      T u[KP];
+#pragma unroll
+      for (int k = 0; k < KP; ++k) u[k] = T(0);
+      const T* zr = tile + tid * ld;
+#pragma unroll 4
+      for (int cc = 0; cc < Khat; ++cc) {
+        const T z = zr[cc];
+        const V* v = reinterpret_cast<const V*>(vs + cc * KP);
+#pragma unroll
+        for (int q = 0; q < KP / W; ++q) {
+          const V x = v[q];
+          if constexpr (sizeof(T) == 4) {
+            u[4 * q + 0] = fma(z, x.x, u[4 * q + 0]);
+            u[4 * q + 1] = fma(z, x.y, u[4 * q + 1]);
+            u[4 * q + 2] = fma(z, x.z, u[4 * q + 2]);
+            u[4 * q + 3] = fma(z, x.w, u[4 * q + 3]);
+          } else {
+            u[2 * q + 0] = fma(z, x.x, u[2 * q + 0]);
+            u[2 * q + 1] = fma(z, x.y, u[2 * q + 1]);
+          }
+        }
+      }
+      T* ur = U + (int64_t)(r0 + tid) * K;
+#pragma unroll
+      for (int k = 0; k < KM; ++k)
+        if (k < K) ur[k] = u[k];
+      if (GRAM) {
+        int q = 0;
+#pragma unroll
+        for (int x = 0; x < KM; ++x)
+#pragma unroll
+          for (int y = x; y < KM; ++y) {
+            g[q] = fma(u[x], u[y], g[q]);
+            ++q;
+          }
+      }
+    }
+  }
+  if (GRAM) {
+    const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      T v = g[q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) wsum[w][q] = v;
+    }
+    __syncthreads();
+    for (int q = tid; q < NP; q += 128) {
+      int x = 0, rem = q;
+      while (rem >= KM - x) {
+        rem -= KM - x;
+        ++x;
+      }
+      const int y = x + rem;
+      if (x < K && y < K) {
+        const double sum = (double)wsum[0][q] + (double)wsum[1][q] + (double)wsum[2][q] + (double)wsum[3][q];
+        Cpart[(int64_t)blockIdx.x * K * K + x * K + y] = sum;
+        Cpart[(int64_t)blockIdx.x * K * K + y * K + x] = sum;
+      }
+    }
+  }
+}
+
 // ------------------------------------------------------------------ CholeskyQR2
 // Per-block partial of (U M)^T (U M): batches of 64 rows are transformed into
 // shared memory, each thread sums its (a,b) pairs over a batch in T and adds
@@ -580,6 +708,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_small_gram(const T* __restrict__ U, int R, int K, const double* __restrict__ M,
                                                     double* __restrict__ Cpart) {
   __shared__ T rows[64][TK_MAXK + 1];
+  __shared__ T raw[64][TK_MAXK + 1];
   __shared__ T Ms[TK_MAXK][TK_MAXK];
   __shared__ unsigned char pa[TK_MAXK * (TK_MAXK + 1) / 2], pb[TK_MAXK * (TK_MAXK + 1) / 2];
   const int tid = threadIdx.x;
@@ -600,16 +729,19 @@ __global__ void __launch_bounds__(256) k_small_gram(const T* __restrict__ U, int
   __syncthreads();
   for (int b = blockIdx.x; b < nbatch; b += gridDim.x) {
     const int r0 = b * 64;
+    for (int i = tid; i < 64 * K; i += 256) {  // raw rows, coalesced
+      const int r = i / K, k = i - r * K;
+      raw[r][k] = (r0 + r < R) ? U[(int64_t)r0 * K + i] : T(0);
+    }
+    __syncthreads();
     for (int i = tid; i < 64 * K; i += 256) {
       const int r = i / K, k = i - r * K;
-      const int row = r0 + r;
-      T v = T(0);
-      if (row < R) {
-        if (M) {
-          for (int j = 0; j <= k; ++j) v = fma(U[(int64_t)row * K + j], Ms[j][k], v);  // M upper triangular
-        } else {
-          v = U[(int64_t)row * K + k];
-        }
+      T v;
+      if (M) {
+        v = T(0);
+        for (int j = 0; j <= k; ++j) v = fma(raw[r][j], Ms[j][k], v);  // M upper triangular
+      } else {
+        v = raw[r][k];
       }
       rows[r][k] = v;
     }
@@ -634,18 +766,89 @@ __global__ void __launch_bounds__(256) k_small_gram(const T* __restrict__ U, int
   }
 }
 
-// C = sum of the block partials (fixed order); C = R^T R; out = prev * R^-1.
-// One warp: lanes over rows / columns.
-__global__ void k_chol_inv(const double* __restrict__ Cpart, int nblk, int K, const double* prev, double* out, int* err) {
+// Second CholeskyQR Gram, thread per row: v = u M (M upper triangular),
+// v v^T accumulated in registers over the thread's rows; warp sums, then one
+// FP64 partial per block.
+template <typename T, int KM>
+__global__ void __launch_bounds__(256) k_row_gram(const T* __restrict__ U, int R, int K, const double* __restrict__ M,
+                                                  double* __restrict__ Cpart) {
+  constexpr int NP = KM * (KM + 1) / 2;
+  __shared__ T Ms[KM][KM];
+  __shared__ T wsum[8][NP];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < KM * KM; i += 256) {
+    const int r = i / KM, cc = i - r * KM;
+    Ms[r][cc] = (r < K && cc < K) ? (T)M[r * K + cc] : T(0);
+  }
+  __syncthreads();
+  T g[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) g[q] = T(0);
+  for (int r = blockIdx.x * 256 + tid; r < R; r += gridDim.x * 256) {
+    T u[KM], v[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) u[k] = k < K ? U[(int64_t)r * K + k] : T(0);
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      T acc = T(0);
+#pragma unroll
+      for (int j = 0; j <= k; ++j) acc = fma(u[j], Ms[j][k], acc);
+      v[k] = acc;
+    }
+    int q = 0;
+#pragma unroll
+    for (int x = 0; x < KM; ++x)
+#pragma unroll
+      for (int y = x; y < KM; ++y) {
+        g[q] = fma(v[x], v[y], g[q]);
+        ++q;
+      }
+  }
+  const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    T x = g[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) wsum[w][q] = x;
+  }
+  __syncthreads();
+  for (int q = tid; q < NP; q += 256) {
+    int x = 0, rem = q;
+    while (rem >= KM - x) {
+      rem -= KM - x;
+      ++x;
+    }
+    const int y = x + rem;
+    if (x < K && y < K) {
+      double sum = 0.0;
+      for (int ww = 0; ww < 8; ++ww) sum += (double)wsum[ww][q];
+      Cpart[(int64_t)blockIdx.x * K * K + x * K + y] = sum;
+      Cpart[(int64_t)blockIdx.x * K * K + y * K + x] = sum;
+    }
+  }
+}
+
+// C = sum of the block partials (8 lanes per entry, fixed shuffle tree);
+// C = R^T R; out = prev * R^-1.  The factorisation runs on warp 0.
+__global__ void __launch_bounds__(1024) k_chol_inv(const double* __restrict__ Cpart, int nblk, int K,
+                                                   const double* prev, double* out, int* err) {
   __shared__ double C[TK_MAXK][TK_MAXK + 1];
   __shared__ double Ri[TK_MAXK][TK_MAXK + 1];
-  const int lane = threadIdx.x;
-  for (int i = lane; i < K * K; i += 32) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int part = tid & 7;
+  for (int base = 0; base < K * K; base += 1024 >> 3) {  // uniform trip count for every lane
+    const int e = base + (tid >> 3);
     double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += Cpart[(int64_t)b * K * K + i];
-    C[i / K][i % K] = s;
+    if (e < K * K)
+      for (int b = part; b < nblk; b += 8) s += Cpart[(int64_t)b * K * K + e];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (part == 0 && e < K * K) C[e / K][e % K] = s;
   }
-  __syncwarp();
+  __syncthreads();
+  if (tid >= 32) return;
   // Cholesky C = L L^T in place (lower); R = L^T
   bool bad = false;
   for (int j = 0; j < K; ++j) {
@@ -744,15 +947,23 @@ __global__ void __launch_bounds__(256) k_apply(T* __restrict__ U, int R, int K, 
 }
 
 __global__ void k_signs(const double* colbest, int nblk, int K, double* sign) {
-  const int k = threadIdx.x;
+  const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (k >= K) return;
   Cand<double> c{-1.0, 0x7fffffff, 0.0};
-  for (int b = 0; b < nblk; ++b) {
+  for (int b = lane; b < nblk; b += 32) {
     const double* o = colbest + ((int64_t)b * K + k) * 3;
     const Cand<double> d{o[0], (int)o[1], o[2]};
     if (better(d, c)) c = d;
   }
-  sign[k] = c.v < 0.0 ? -1.0 : 1.0;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    Cand<double> d;
+    d.a = __shfl_xor_sync(0xffffffffu, c.a, o);
+    d.r = __shfl_xor_sync(0xffffffffu, c.r, o);
+    d.v = __shfl_xor_sync(0xffffffffu, c.v, o);
+    if (better(d, c)) c = d;
+  }
+  if (lane == 0) sign[k] = c.v < 0.0 ? -1.0 : 1.0;
 }
 
 template <typename T>
@@ -763,6 +974,11 @@ __global__ void k_scatter_rows(const T* __restrict__ U, int R, int K, const int3
     const int r = (int)(i / K), k = (int)(i - (int64_t)r * K);
     F[(int64_t)row_id[r] * ldF + k] = (T)(sign[k] * (double)U[i]);
   }
+}
+
+template <typename Kern>
+void set_tile_attr(Kern k, size_t bytes) {
+  TK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(bytes, 48 * 1024)));
 }
 
 template <typename T>
@@ -804,7 +1020,7 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
       k_gram<T, 64><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
     }
     TK_CUDA(cudaGetLastError());
-    const unsigned g2 = (unsigned)std::min<int64_t>(tk_ceil_div((int64_t)Khat * Khat, 256), 4096);
+    const unsigned g2 = (unsigned)std::min<int64_t>(tk_ceil_div((int64_t)Khat * Khat * 8, 256), 8192);
     k_gram_reduce<T><<<g2, 256, 0, s>>>((const T*)c->Wpart, nsplit, ntiles, tpd, TM, Khat, c->W);
     TK_CUDA(cudaGetLastError());
     tk_launched(c, PH_GRAM, 2);
@@ -845,22 +1061,46 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
   {
     const T* Vs = (const T*)c->Vs;
     T* U = (T*)c->U;
-    const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), 8 * sms));
-    if (K <= 8) k_backproj<T, 8><<<gb, 256, 0, s>>>(Z, R, Khat, Vs, K, U);
-    else if (K <= 16) k_backproj<T, 16><<<gb, 256, 0, s>>>(Z, R, Khat, Vs, K, U);
-    else k_backproj<T, 32><<<gb, 256, 0, s>>>(Z, R, Khat, Vs, K, U);
-    TK_CUDA(cudaGetLastError());
-    const int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 64), 2 * sms));
     double* R1 = c->Rinv;
     double* R2 = c->Rinv + TK_MAXK * TK_MAXK;
     double* sign = c->Rinv + 2 * TK_MAXK * TK_MAXK;
-    k_small_gram<T><<<nblk, 256, 0, s>>>(U, R, K, nullptr, c->Cpart);
-    k_chol_inv<<<1, 32, 0, s>>>(c->Cpart, nblk, K, nullptr, R1, c->err);
-    k_small_gram<T><<<nblk, 256, 0, s>>>(U, R, K, R1, c->Cpart);
-    k_chol_inv<<<1, 32, 0, s>>>(c->Cpart, nblk, K, R1, R2, c->err);
+    const size_t tshm = ((size_t)Khat * 16 + (size_t)128 * (Khat + 1)) * sizeof(T);
+    int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 128), 4 * sms));
+    if (K <= (sizeof(T) == 4 ? 16 : 12) && tshm <= 200 * 1024) {
+      // tiled back-projection fused with the first CholeskyQR Gram
+      if (K <= 8) {
+        set_tile_attr(k_backproj_tile<T, 8, true>, tshm);
+        k_backproj_tile<T, 8, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, c->Cpart);
+      } else if (K <= 12) {
+        set_tile_attr(k_backproj_tile<T, 12, true>, tshm);
+        k_backproj_tile<T, 12, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, c->Cpart);
+      } else if constexpr (sizeof(T) == 4) {
+        set_tile_attr(k_backproj_tile<T, 16, true>, tshm);
+        k_backproj_tile<T, 16, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, c->Cpart);
+      }
+      TK_CUDA(cudaGetLastError());
+    } else {
+      const unsigned gb = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), 8 * sms));
+      if (K <= 8) k_backproj<T, 8><<<gb, 256, 0, s>>>(Z, R, Khat, Vs, K, U);
+      else if (K <= 16) k_backproj<T, 16><<<gb, 256, 0, s>>>(Z, R, Khat, Vs, K, U);
+      else k_backproj<T, 32><<<gb, 256, 0, s>>>(Z, R, Khat, Vs, K, U);
+      TK_CUDA(cudaGetLastError());
+      nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 64), 2 * sms));
+      k_small_gram<T><<<nblk, 256, 0, s>>>(U, R, K, nullptr, c->Cpart);
+    }
+    k_chol_inv<<<1, 1024, 0, s>>>(c->Cpart, nblk, K, nullptr, R1, c->err);
+    nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 64), 2 * sms));
+    if (K <= (sizeof(T) == 4 ? 12 : 8)) {
+      nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), 4 * sms));
+      if (K <= 8) k_row_gram<T, 8><<<nblk, 256, 0, s>>>(U, R, K, R1, c->Cpart);
+      else if constexpr (sizeof(T) == 4) k_row_gram<T, 12><<<nblk, 256, 0, s>>>(U, R, K, R1, c->Cpart);
+    } else {
+      k_small_gram<T><<<nblk, 256, 0, s>>>(U, R, K, R1, c->Cpart);
+    }
+    k_chol_inv<<<1, 1024, 0, s>>>(c->Cpart, nblk, K, R1, R2, c->err);
     const int nab = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), 2 * sms));
     k_apply<T><<<nab, 256, 0, s>>>(U, R, K, R2, c->colbest);
-    k_signs<<<1, 32, 0, s>>>(c->colbest, nab, K, sign);
+    k_signs<<<1, 32 * K, 0, s>>>(c->colbest, nab, K, sign);
     TK_CUDA(cudaMemsetAsync(F_out, 0, (size_t)c->L[n] * ldF_out * sizeof(T), s));
     const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div((int64_t)R * K, 256), 8 * sms));
     k_scatter_rows<T><<<gs, 256, 0, s>>>(U, R, K, md.row_id, sign, (T*)F_out, ldF_out);
