@@ -40,6 +40,7 @@ void check_device_error(tucker_ctx* c, cudaStream_t s) {
     if (h & TK_DEV_ERR_NUMERIC) tk_throw(TUCKER_ERR_NUMERIC, "numeric breakdown (rank-deficient factor update)");
     if (h & TK_DEV_ERR_NONFINITE) tk_throw(TUCKER_ERR_ARG, "non-finite tensor value");
     if (h & TK_DEV_ERR_INDEX) tk_throw(TUCKER_ERR_INDEX, "coordinate out of range");
+    if (h & TK_DEV_ERR_TIMEOUT) tk_throw(TUCKER_ERR_TIMEOUT, "a bounded device wait ran out");
     tk_throw(TUCKER_ERR_STATE, "device error word " + std::to_string(h));
   }
 }

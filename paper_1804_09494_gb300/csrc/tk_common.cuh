@@ -23,6 +23,7 @@
 #define TK_DEV_ERR_NUMERIC 2
 #define TK_DEV_ERR_NONFINITE 4
 #define TK_DEV_ERR_LIMIT 8
+#define TK_DEV_ERR_TIMEOUT 16
 
 enum tk_phase { PH_TTM = 0, PH_FIXUP, PH_GRAM, PH_EIG, PH_BACKPROJ, PH_CORE, PH_BWD, PH_OTHER, PH_COUNT };
 
@@ -158,6 +159,10 @@ void tk_ttmc_forward(tucker_ctx* c, int n, void* const* F, const int* ldF, const
                      cudaStream_t s);
 void tk_ttmc_backward(tucker_ctx* c, int n, void* const* F, const int* ldF, const void* dZ,
                       const void* vals_override, void* const* dF, void* dval, cudaStream_t s);
+
+// ---- Gram on the tensor cores (tk_gram_tc.cu) ----
+bool tk_gram_tc_supported(int Khat);
+int tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, size_t Wpart_elems, cudaStream_t s);
 
 // ---- factor update (tk_factor.cu) ----
 void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, double* sigma_out,

@@ -999,7 +999,19 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
 
   // ---- Gram W = Z^T Z
   tk_phase_begin(c, PH_GRAM, s);
-  {
+  bool gram_done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (tk_gram_tc_supported(Khat) && ((uintptr_t)Z % 16 == 0)) {
+      // tensor cores: per-CTA partials of the full 128 x 128 tile, reduced in FP64
+      const int nsplit = tk_gram_tc(c, (const float*)Z, R, Khat, (float*)c->Wpart, c->Wpart_elems, s);
+      const unsigned g2 = (unsigned)std::min<int64_t>(tk_ceil_div((int64_t)Khat * Khat * 8, 256), 8192);
+      k_gram_reduce<T><<<g2, 256, 0, s>>>((const T*)c->Wpart, nsplit, 1, 1, 128, Khat, c->W);
+      TK_CUDA(cudaGetLastError());
+      tk_launched(c, PH_GRAM, 2);
+      gram_done = true;
+    }
+  }
+  if (!gram_done) {
     const int TM = (sizeof(T) == 4 && Khat > 64) ? 128 : 64;
     const int tpd = (int)tk_ceil_div(Khat, TM);
     const int ntiles = tpd * (tpd + 1) / 2;
