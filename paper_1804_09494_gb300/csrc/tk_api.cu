@@ -48,6 +48,11 @@ void check_device_error(tucker_ctx* c, cudaStream_t s) {
 void release(tucker_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  for (int n = 0; n < TK_MAXN; ++n) {
+    if (c->aux[n]) cudaStreamDestroy(c->aux[n]);
+    if (c->ev_ttm[n]) cudaEventDestroy(c->ev_ttm[n]);
+    if (c->ev_fu[n]) cudaEventDestroy(c->ev_fu[n]);
+  }
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   if (c->timing)
@@ -241,26 +246,18 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
       gp = std::max(gp, (size_t)ns * c->K[n] * md.Khat);
     }
     const size_t esz = c->esz;
-    c->Z = tk_alloc(c, zc * esz);
+    for (int n = 0; n < N; ++n) {
+      c->Zm[n] = tk_alloc(c, (size_t)std::max(c->mode[n].R, 1) * c->mode[n].Khat * esz);
+      tk_alloc_fuws(c, n);
+      TK_CUDA(cudaStreamCreateWithFlags(&c->aux[n], cudaStreamNonBlocking));
+      TK_CUDA(cudaEventCreateWithFlags(&c->ev_ttm[n], cudaEventDisableTiming));
+      TK_CUDA(cudaEventCreateWithFlags(&c->ev_fu[n], cudaEventDisableTiming));
+    }
+    (void)zc;
+    (void)wp;
+    (void)tiles_cap;
     c->Zpart = tk_alloc(c, zp * esz);
     c->Zchunk = (double*)tk_alloc(c, std::max<size_t>(zch, 1) * 8);
-    c->Wpart = tk_alloc(c, wp * esz);
-    c->Wpart_elems = wp;
-    c->gram_tiles = (int2*)tk_alloc(c, (size_t)tiles_cap * sizeof(int2));
-    c->gram_tiles_cap = tiles_cap;
-    c->W = (double*)tk_alloc(c, (size_t)c->maxKhat * c->maxKhat * 8);
-    c->eigA = tk_alloc(c, (size_t)c->maxKhat * c->maxKhat * esz);
-    c->eigV = tk_alloc(c, (size_t)c->maxKhat * c->maxKhat * esz);
-    c->eigX = (double*)tk_alloc(c, (size_t)2 * c->maxKhat * c->Kmax * 8);
-    c->eigAB = (double*)tk_alloc(c, (size_t)2 * c->maxKhat * 8);
-    c->eigTri = tk_alloc(c, (size_t)6 * c->Kmax * c->maxKhat * esz);
-    c->Vs = tk_alloc(c, (size_t)c->maxKhat * c->Kmax * esz);
-    c->V = (double*)tk_alloc(c, (size_t)c->maxKhat * c->Kmax * 8);
-    c->sigma = (double*)tk_alloc(c, (size_t)TK_MAXK * 8);
-    c->U = tk_alloc(c, (size_t)c->maxR * c->Kmax * esz);
-    c->Cpart = (double*)tk_alloc(c, (size_t)4 * c->sm_count * TK_MAXK * TK_MAXK * 8);
-    c->Rinv = (double*)tk_alloc(c, (size_t)3 * TK_MAXK * TK_MAXK * 8);
-    c->colbest = (double*)tk_alloc(c, (size_t)2 * c->sm_count * TK_MAXK * 3 * 8);
     c->Gpart = (double*)tk_alloc(c, gp * 8);
     c->Gd = (double*)tk_alloc(c, (size_t)c->Gsize * 8);
     c->fit_d = (double*)tk_alloc(c, 4 * 8);
@@ -339,11 +336,26 @@ tucker_status hooi_iter(tucker_t t, void* const* d_F, void* d_G, double* h_fit, 
     check_ctx(t);
     cudaStream_t s = (cudaStream_t)stream;
     copy_in_factors(t, (const void* const*)d_F, -1, s);
-    for (int n = 0; n < t->N; ++n) {
-      void* src[TK_MAXN];
-      for (int m = 0; m < t->N; ++m) src[m] = (t->gauss_seidel && m < n) ? t->Fb[m] : t->Fa[m];
-      tk_ttmc_forward(t, n, src, t->ldF, nullptr, t->Z, s);
-      tk_factor_update(t, n, t->Z, t->Fb[n], t->ldF[n], nullptr, s);
+    if (t->gauss_seidel) {
+      // each mode sees the factors refined so far: strictly sequential
+      for (int n = 0; n < t->N; ++n) {
+        void* src[TK_MAXN];
+        for (int m = 0; m < t->N; ++m) src[m] = m < n ? t->Fb[m] : t->Fa[m];
+        tk_ttmc_forward(t, n, src, t->ldF, nullptr, t->Zm[n], s);
+        tk_factor_update(t, n, t->Zm[n], t->Fb[n], t->ldF[n], nullptr, s);
+      }
+    } else {
+      // Fig. 1 as printed: every TTM-chain reads the input factors, so the
+      // factor update of mode n (side stream n) overlaps the TTM-chains of the
+      // later modes on the caller's stream.
+      for (int n = 0; n < t->N; ++n) {
+        tk_ttmc_forward(t, n, t->Fa, t->ldF, nullptr, t->Zm[n], s);
+        TK_CUDA(cudaEventRecord(t->ev_ttm[n], s));
+        TK_CUDA(cudaStreamWaitEvent(t->aux[n], t->ev_ttm[n], 0));
+        tk_factor_update(t, n, t->Zm[n], t->Fb[n], t->ldF[n], nullptr, t->aux[n]);
+        TK_CUDA(cudaEventRecord(t->ev_fu[n], t->aux[n]));
+      }
+      for (int n = 0; n < t->N; ++n) TK_CUDA(cudaStreamWaitEvent(s, t->ev_fu[n], 0));
     }
     tk_core(t, t->Fb, t->ldF, d_G, s);
     for (int m = 0; m < t->N; ++m) tk_copy_factor(t, t->Fb[m], t->ldF[m], d_F[m], t->K[m], t->L[m], t->K[m], s);

@@ -70,6 +70,27 @@ struct tk_buf {
   size_t bytes = 0;
 };
 
+// Scratch of one factor update (Gram, eigensolve, back-projection, CholeskyQR2).
+struct tk_fuws {
+  void* Wpart = nullptr;    // Gram split partials
+  size_t Wpart_elems = 0;
+  double* W = nullptr;      // Khat x Khat
+  int2* gram_tiles = nullptr;
+  int gram_tiles_cap = 0;
+  double* eigX = nullptr;   // 2 x Khat x K
+  double* eigAB = nullptr;  // 2 x Khat
+  void* eigTri = nullptr;   // K x 6 x Khat (T)
+  void* Vs = nullptr;       // Khat x K (T)
+  double* V = nullptr;      // Khat x K
+  double* sigma = nullptr;  // TK_MAXK
+  void* eigA = nullptr;     // Khat x Khat (T)
+  void* eigV = nullptr;     // Khat x Khat (T)
+  void* U = nullptr;        // R x K (T)
+  double* Cpart = nullptr;  // 4 * SMs x TK_MAXK^2
+  double* Rinv = nullptr;   // 3 x TK_MAXK^2
+  double* colbest = nullptr;// 2 * SMs x TK_MAXK x 3
+};
+
 struct tucker_ctx {
   int N = 0;
   int64_t L[TK_MAXN] = {};
@@ -93,23 +114,11 @@ struct tucker_ctx {
   void* Z = nullptr;        // max_n R_n * Khat_n
   void* Zpart = nullptr;    // max_n 2 * P_n * Khat_n
   double* Zchunk = nullptr; // max_n nchunks * Khat_n
-  void* Wpart = nullptr;    // Gram split partials
-  size_t Wpart_elems = 0;
-  double* W = nullptr;      // Khat x Khat
-  int2* gram_tiles = nullptr; // upper-triangle tile list
-  int gram_tiles_cap = 0;
-  double* eigX = nullptr;   // 2 x Khat x Kmax (eigensolver scratch)
-  double* eigAB = nullptr;  // 2 x Khat (Lanczos tridiagonal)
-  void* eigTri = nullptr;   // Kmax x 6 x Khat (T): tridiagonal LU + inverse-iteration vectors
-  void* Vs = nullptr;       // Khat x Kmax (T): V Sigma^-1
-  double* V = nullptr;      // Khat x Kmax (eigenvectors)
-  double* sigma = nullptr;  // Kmax
-  void* eigA = nullptr;     // Jacobi work matrix (T) Khat x Khat
-  void* eigV = nullptr;     // Jacobi vectors (T) Khat x Khat
-  void* U = nullptr;        // max R_n * Kmax (T)
-  double* Cpart = nullptr;  // blocks * Kmax^2
-  double* Rinv = nullptr;   // Kmax^2 x 2
-  double* colbest = nullptr;// blocks * Kmax * 2 (value, row) candidates
+  tk_fuws fu[TK_MAXN];      // factor-update workspace, one per mode (modes overlap on side streams)
+  void* Zm[TK_MAXN] = {};   // per-mode penultimate matrices (R_n x Khat_n)
+  cudaStream_t aux[TK_MAXN] = {};
+  cudaEvent_t ev_ttm[TK_MAXN] = {};
+  cudaEvent_t ev_fu[TK_MAXN] = {};
   double* Gpart = nullptr;  // core partials
   double* Gd = nullptr;     // core (double) prod K
   double* fit_d = nullptr;  // [0] = ||G||^2, [1] = fit
@@ -167,6 +176,7 @@ int tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, siz
 // ---- factor update (tk_factor.cu) ----
 void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, double* sigma_out,
                       cudaStream_t s);
+void tk_alloc_fuws(tucker_ctx* c, int n);
 
 // ---- core / fit (tk_core.cu) ----
 void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s);

@@ -141,14 +141,14 @@ void core_impl(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaS
   }
   const int n = best;
   const tk_mode& md = c->mode[n];
-  tk_ttmc_forward(c, n, F, ldF, nullptr, c->Z, s);
+  tk_ttmc_forward(c, n, F, ldF, nullptr, c->Zm[n], s);
   tk_phase_begin(c, PH_CORE, s);
   const int K = c->K[n], Khat = md.Khat, R = md.R;
   const int cb = (int)tk_ceil_div(Khat, 128);
   int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), tk_ceil_div(4 * c->sm_count, cb)));
   const int rps = (int)tk_ceil_div(R, nsplit);
   dim3 grid(cb, nsplit);
-  const T* Z = (const T*)c->Z;
+  const T* Z = (const T*)c->Zm[n];
   const T* Fn = (const T*)F[n];
   if (K <= 8) k_core_partial<T, 8><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
   else if (K <= 16) k_core_partial<T, 16><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);

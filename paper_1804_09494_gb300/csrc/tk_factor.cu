@@ -188,6 +188,61 @@ __device__ void reorth_pass(const T* Q, int n, int j, T* w, T* h) {
   __syncthreads();
 }
 
+// FP32 variant with 16-byte shared-memory reads (n % 4 == 0): warp per q_k for
+// the dots; for the update, warp per quad of rows with lanes over k.
+__device__ void reorth_pass_v4(const float* Q, int n, int j, float* w, float* h) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int n4 = n >> 2;
+  const float4* w4 = reinterpret_cast<const float4*>(w);
+  for (int k = wid; k <= j; k += nw) {
+    const float4* q4 = reinterpret_cast<const float4*>(Q + (size_t)k * n);
+    float d = 0.f;
+    for (int i = lane; i < n4; i += 32) {
+      const float4 a = q4[i], b = w4[i];
+      d = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, d))));
+    }
+    d = warp_allsum(d);
+    if (lane == 0) h[k] = d;
+  }
+  __syncthreads();
+  float4* wv = reinterpret_cast<float4*>(w);
+  for (int qd = wid; qd < n4; qd += nw) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int k = lane; k <= j; k += 32) {
+      const float hk = h[k];
+      const float4 q = reinterpret_cast<const float4*>(Q + (size_t)k * n)[qd];
+      acc.x = fmaf(hk, q.x, acc.x);
+      acc.y = fmaf(hk, q.y, acc.y);
+      acc.z = fmaf(hk, q.z, acc.z);
+      acc.w = fmaf(hk, q.w, acc.w);
+    }
+    acc.x = warp_allsum(acc.x);
+    acc.y = warp_allsum(acc.y);
+    acc.z = warp_allsum(acc.z);
+    acc.w = warp_allsum(acc.w);
+    if (lane == 0) {
+      float4 x = wv[qd];
+      x.x -= acc.x;
+      x.y -= acc.y;
+      x.z -= acc.z;
+      x.w -= acc.w;
+      wv[qd] = x;
+    }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ void reorth(const T* Q, int n, int j, T* w, T* h) {
+  if constexpr (sizeof(T) == 4) {
+    if ((n & 3) == 0) {
+      reorth_pass_v4(Q, n, j, w, h);
+      return;
+    }
+  }
+  reorth_pass<T>(Q, n, j, w, h);
+}
+
 // number of eigenvalues of the symmetric tridiagonal (a, b2 = off-diagonal^2) below x
 template <typename T>
 __device__ int sturm_count(const T* a, const T* b2, int m, T x, T pivmin) {
@@ -337,17 +392,37 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   }
   for (int j = 0; j < m; ++j) {
     const T* qj = Q + (size_t)j * n;
-    for (int r = wid; r < n; r += nw) {  // w = A q_j, warp per row
-      const T* ar = A + (size_t)r * n;
-      T sacc = T(0);
-      for (int cidx = lane; cidx < n; cidx += 32) sacc = fma(ar[cidx], qj[cidx], sacc);
-      sacc = warp_allsum(sacc);
-      if (lane == 0) w[r] = sacc;
+    bool vec_done = false;
+    if constexpr (sizeof(T) == 4) {
+      if ((n & 3) == 0) {  // w = A q_j, warp per row, 16-byte reads
+        const int n4 = n >> 2;
+        const float4* q4 = reinterpret_cast<const float4*>(qj);
+        for (int r = wid; r < n; r += nw) {
+          const float4* a4 = reinterpret_cast<const float4*>(A + (size_t)r * n);
+          float sacc = 0.f;
+          for (int i = lane; i < n4; i += 32) {
+            const float4 x = a4[i], y = q4[i];
+            sacc = fmaf(x.x, y.x, fmaf(x.y, y.y, fmaf(x.z, y.z, fmaf(x.w, y.w, sacc))));
+          }
+          sacc = warp_allsum(sacc);
+          if (lane == 0) w[r] = sacc;
+        }
+        vec_done = true;
+      }
+    }
+    if (!vec_done) {
+      for (int r = wid; r < n; r += nw) {  // w = A q_j, warp per row
+        const T* ar = A + (size_t)r * n;
+        T sacc = T(0);
+        for (int cidx = lane; cidx < n; cidx += 32) sacc = fma(ar[cidx], qj[cidx], sacc);
+        sacc = warp_allsum(sacc);
+        if (lane == 0) w[r] = sacc;
+      }
     }
     __syncthreads();
-    reorth_pass<T>(Q, n, j, w, h);
+    reorth<T>(Q, n, j, w, h);
     T al = h[j];
-    reorth_pass<T>(Q, n, j, w, h);
+    reorth<T>(Q, n, j, w, h);
     al += h[j];
     if (tid == 0) ta[j] = al;
     T nn = T(0);
@@ -364,8 +439,8 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
       if (tid == 0) tb[j] = T(0);
       for (int i = tid; i < n; i += nt) w[i] = hash_unit<T>(j + 2, i);
       __syncthreads();
-      reorth_pass<T>(Q, n, j, w, h);
-      reorth_pass<T>(Q, n, j, w, h);
+      reorth<T>(Q, n, j, w, h);
+      reorth<T>(Q, n, j, w, h);
       T n2 = T(0);
       for (int i = tid; i < n; i += nt) n2 = fma(w[i], w[i], n2);
       n2 = block_sum<T>(n2, red);
@@ -993,6 +1068,7 @@ void setup_eig_attr() {
 template <typename T>
 void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out, double* sigma_out, cudaStream_t s) {
   const tk_mode& md = c->mode[n];
+  tk_fuws* ws = &c->fu[n];
   const int R = md.R, Khat = md.Khat, K = c->K[n];
   const T* Z = (const T*)Zv;
   const int sms = c->sm_count;
@@ -1003,9 +1079,9 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
   if constexpr (sizeof(T) == 4) {
     if (tk_gram_tc_supported(Khat) && ((uintptr_t)Z % 16 == 0)) {
       // tensor cores: per-CTA partials of the full 128 x 128 tile, reduced in FP64
-      const int nsplit = tk_gram_tc(c, (const float*)Z, R, Khat, (float*)c->Wpart, c->Wpart_elems, s);
+      const int nsplit = tk_gram_tc(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->Wpart_elems, s);
       const unsigned g2 = (unsigned)std::min<int64_t>(tk_ceil_div((int64_t)Khat * Khat * 8, 256), 8192);
-      k_gram_reduce<T><<<g2, 256, 0, s>>>((const T*)c->Wpart, nsplit, 1, 1, 128, Khat, c->W);
+      k_gram_reduce<T><<<g2, 256, 0, s>>>((const T*)ws->Wpart, nsplit, 1, 1, 128, Khat, ws->W);
       TK_CUDA(cudaGetLastError());
       tk_launched(c, PH_GRAM, 2);
       gram_done = true;
@@ -1016,24 +1092,24 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     const int tpd = (int)tk_ceil_div(Khat, TM);
     const int ntiles = tpd * (tpd + 1) / 2;
     int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 64), tk_ceil_div(2 * sms, ntiles)));
-    while ((size_t)nsplit * ntiles * TM * TM > c->Wpart_elems && nsplit > 1) --nsplit;
+    while ((size_t)nsplit * ntiles * TM * TM > ws->Wpart_elems && nsplit > 1) --nsplit;
     const int rps = (int)tk_ceil_div(R, nsplit);
     std::vector<int2> tl;
     for (int i = 0; i < tpd; ++i)
       for (int j = i; j < tpd; ++j) tl.push_back(make_int2(i, j));
-    if ((int)tl.size() > c->gram_tiles_cap) tk_throw(TUCKER_ERR_STATE, "internal: Gram tile list too long");
-    int2* dtiles = c->gram_tiles;
+    if ((int)tl.size() > ws->gram_tiles_cap) tk_throw(TUCKER_ERR_STATE, "internal: Gram tile list too long");
+    int2* dtiles = ws->gram_tiles;
     TK_CUDA(cudaMemcpyAsync(dtiles, tl.data(), tl.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     dim3 grid(ntiles, nsplit);
     if constexpr (sizeof(T) == 4) {
-      if (TM == 128) k_gram<T, 128><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
-      else k_gram<T, 64><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
+      if (TM == 128) k_gram<T, 128><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)ws->Wpart);
+      else k_gram<T, 64><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)ws->Wpart);
     } else {
-      k_gram<T, 64><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)c->Wpart);
+      k_gram<T, 64><<<grid, 256, 0, s>>>(Z, R, Khat, dtiles, ntiles, rps, (T*)ws->Wpart);
     }
     TK_CUDA(cudaGetLastError());
     const unsigned g2 = (unsigned)std::min<int64_t>(tk_ceil_div((int64_t)Khat * Khat * 8, 256), 8192);
-    k_gram_reduce<T><<<g2, 256, 0, s>>>((const T*)c->Wpart, nsplit, ntiles, tpd, TM, Khat, c->W);
+    k_gram_reduce<T><<<g2, 256, 0, s>>>((const T*)ws->Wpart, nsplit, ntiles, tpd, TM, Khat, ws->W);
     TK_CUDA(cudaGetLastError());
     tk_launched(c, PH_GRAM, 2);
   }
@@ -1044,23 +1120,23 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
   {
     setup_eig_attr<T>();
     EigArgs<T> a{};
-    a.W = c->W;
+    a.W = ws->W;
     a.n = Khat;
     a.K = K;
-    a.gA = (T*)c->eigA;
-    a.gQ = (T*)c->eigV;
+    a.gA = (T*)ws->eigA;
+    a.gQ = (T*)ws->eigV;
     const size_t mat = (size_t)2 * Khat * Khat * sizeof(T);
     const size_t work = (size_t)5 * Khat * sizeof(T) + 64;
     a.use_smem = (mat + work) <= 150 * 1024;
     const size_t shm = (a.use_smem ? mat : 0) + work;
     a.polish = c->prec == TUCKER_FP32;
-    a.X = c->eigX;
-    a.Y = c->eigX + (size_t)Khat * K;
-    a.ab = c->eigAB;
-    a.tri = (T*)c->eigTri;
-    a.Vout = c->V;
-    a.sigma = c->sigma;
-    a.Vs = (T*)c->Vs;
+    a.X = ws->eigX;
+    a.Y = ws->eigX + (size_t)Khat * K;
+    a.ab = ws->eigAB;
+    a.tri = (T*)ws->eigTri;
+    a.Vout = ws->V;
+    a.sigma = ws->sigma;
+    a.Vs = (T*)ws->Vs;
     a.err = c->err;
     k_eig<T><<<1, 1024, shm, s>>>(a);
     TK_CUDA(cudaGetLastError());
@@ -1071,24 +1147,24 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
   // ---- back-projection + CholeskyQR2 + signs + scatter
   tk_phase_begin(c, PH_BACKPROJ, s);
   {
-    const T* Vs = (const T*)c->Vs;
-    T* U = (T*)c->U;
-    double* R1 = c->Rinv;
-    double* R2 = c->Rinv + TK_MAXK * TK_MAXK;
-    double* sign = c->Rinv + 2 * TK_MAXK * TK_MAXK;
+    const T* Vs = (const T*)ws->Vs;
+    T* U = (T*)ws->U;
+    double* R1 = ws->Rinv;
+    double* R2 = ws->Rinv + TK_MAXK * TK_MAXK;
+    double* sign = ws->Rinv + 2 * TK_MAXK * TK_MAXK;
     const size_t tshm = ((size_t)Khat * 16 + (size_t)128 * (Khat + 1)) * sizeof(T);
     int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 128), 4 * sms));
     if (K <= (sizeof(T) == 4 ? 16 : 12) && tshm <= 200 * 1024) {
       // tiled back-projection fused with the first CholeskyQR Gram
       if (K <= 8) {
         set_tile_attr(k_backproj_tile<T, 8, true>, tshm);
-        k_backproj_tile<T, 8, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, c->Cpart);
+        k_backproj_tile<T, 8, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart);
       } else if (K <= 12) {
         set_tile_attr(k_backproj_tile<T, 12, true>, tshm);
-        k_backproj_tile<T, 12, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, c->Cpart);
+        k_backproj_tile<T, 12, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart);
       } else if constexpr (sizeof(T) == 4) {
         set_tile_attr(k_backproj_tile<T, 16, true>, tshm);
-        k_backproj_tile<T, 16, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, c->Cpart);
+        k_backproj_tile<T, 16, true><<<nblk, 128, tshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart);
       }
       TK_CUDA(cudaGetLastError());
     } else {
@@ -1098,27 +1174,27 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
       else k_backproj<T, 32><<<gb, 256, 0, s>>>(Z, R, Khat, Vs, K, U);
       TK_CUDA(cudaGetLastError());
       nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 64), 2 * sms));
-      k_small_gram<T><<<nblk, 256, 0, s>>>(U, R, K, nullptr, c->Cpart);
+      k_small_gram<T><<<nblk, 256, 0, s>>>(U, R, K, nullptr, ws->Cpart);
     }
-    k_chol_inv<<<1, 1024, 0, s>>>(c->Cpart, nblk, K, nullptr, R1, c->err);
+    k_chol_inv<<<1, 1024, 0, s>>>(ws->Cpart, nblk, K, nullptr, R1, c->err);
     nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 64), 2 * sms));
     if (K <= (sizeof(T) == 4 ? 12 : 8)) {
       nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), 4 * sms));
-      if (K <= 8) k_row_gram<T, 8><<<nblk, 256, 0, s>>>(U, R, K, R1, c->Cpart);
-      else if constexpr (sizeof(T) == 4) k_row_gram<T, 12><<<nblk, 256, 0, s>>>(U, R, K, R1, c->Cpart);
+      if (K <= 8) k_row_gram<T, 8><<<nblk, 256, 0, s>>>(U, R, K, R1, ws->Cpart);
+      else if constexpr (sizeof(T) == 4) k_row_gram<T, 12><<<nblk, 256, 0, s>>>(U, R, K, R1, ws->Cpart);
     } else {
-      k_small_gram<T><<<nblk, 256, 0, s>>>(U, R, K, R1, c->Cpart);
+      k_small_gram<T><<<nblk, 256, 0, s>>>(U, R, K, R1, ws->Cpart);
     }
-    k_chol_inv<<<1, 1024, 0, s>>>(c->Cpart, nblk, K, R1, R2, c->err);
+    k_chol_inv<<<1, 1024, 0, s>>>(ws->Cpart, nblk, K, R1, R2, c->err);
     const int nab = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), 2 * sms));
-    k_apply<T><<<nab, 256, 0, s>>>(U, R, K, R2, c->colbest);
-    k_signs<<<1, 32 * K, 0, s>>>(c->colbest, nab, K, sign);
+    k_apply<T><<<nab, 256, 0, s>>>(U, R, K, R2, ws->colbest);
+    k_signs<<<1, 32 * K, 0, s>>>(ws->colbest, nab, K, sign);
     TK_CUDA(cudaMemsetAsync(F_out, 0, (size_t)c->L[n] * ldF_out * sizeof(T), s));
     const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div((int64_t)R * K, 256), 8 * sms));
     k_scatter_rows<T><<<gs, 256, 0, s>>>(U, R, K, md.row_id, sign, (T*)F_out, ldF_out);
     TK_CUDA(cudaGetLastError());
     tk_launched(c, PH_BACKPROJ, 8);
-    if (sigma_out) TK_CUDA(cudaMemcpyAsync(sigma_out, c->sigma, K * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (sigma_out) TK_CUDA(cudaMemcpyAsync(sigma_out, ws->sigma, K * sizeof(double), cudaMemcpyDeviceToDevice, s));
   }
   tk_phase_end(c, s);
 }
@@ -1128,4 +1204,32 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
 void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, double* sigma_out, cudaStream_t s) {
   if (c->prec == TUCKER_FP32) factor_impl<float>(c, n, Z, F_out, ldF_out, sigma_out, s);
   else factor_impl<double>(c, n, Z, F_out, ldF_out, sigma_out, s);
+}
+
+// Per-mode factor-update workspace, sized for that mode.
+void tk_alloc_fuws(tucker_ctx* c, int n) {
+  const tk_mode& md = c->mode[n];
+  tk_fuws& w = c->fu[n];
+  const size_t esz = c->esz;
+  const int Khat = md.Khat, K = c->K[n], sms = c->sm_count;
+  const int TM = (esz == 4 && Khat > 64) ? 128 : 64;
+  const int tpd = (int)tk_ceil_div(Khat, TM);
+  const int ntiles = tpd * (tpd + 1) / 2;
+  w.Wpart_elems = (size_t)(2 * sms + ntiles) * TM * TM;
+  w.Wpart = tk_alloc(c, w.Wpart_elems * esz);
+  w.gram_tiles_cap = ntiles;
+  w.gram_tiles = (int2*)tk_alloc(c, (size_t)ntiles * sizeof(int2));
+  w.W = (double*)tk_alloc(c, (size_t)Khat * Khat * 8);
+  w.eigA = tk_alloc(c, (size_t)Khat * Khat * esz);
+  w.eigV = tk_alloc(c, (size_t)Khat * Khat * esz);
+  w.eigX = (double*)tk_alloc(c, (size_t)2 * Khat * K * 8);
+  w.eigAB = (double*)tk_alloc(c, (size_t)2 * Khat * 8);
+  w.eigTri = tk_alloc(c, (size_t)6 * K * Khat * esz);
+  w.Vs = tk_alloc(c, (size_t)Khat * K * esz);
+  w.V = (double*)tk_alloc(c, (size_t)Khat * K * 8);
+  w.sigma = (double*)tk_alloc(c, (size_t)TK_MAXK * 8);
+  w.U = tk_alloc(c, (size_t)std::max(md.R, 1) * K * esz);
+  w.Cpart = (double*)tk_alloc(c, (size_t)4 * sms * TK_MAXK * TK_MAXK * 8);
+  w.Rinv = (double*)tk_alloc(c, (size_t)3 * TK_MAXK * TK_MAXK * 8);
+  w.colbest = (double*)tk_alloc(c, (size_t)2 * sms * TK_MAXK * 3 * 8);
 }
