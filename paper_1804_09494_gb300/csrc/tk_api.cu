@@ -53,11 +53,36 @@ void release(tucker_ctx* c) {
     if (c->ev_ttm[n]) cudaEventDestroy(c->ev_ttm[n]);
     if (c->ev_fu[n]) cudaEventDestroy(c->ev_fu[n]);
   }
+  for (int m = 0; m < TK_MAXN; ++m) {
+    if (c->texFa[m]) cudaDestroyTextureObject(c->texFa[m]);
+    if (c->texFb[m]) cudaDestroyTextureObject(c->texFb[m]);
+  }
   for (void* p : c->allocs) cudaFree(p);
   c->allocs.clear();
   if (c->timing)
     for (int i = 0; i < 2 * kEvPairs; ++i) cudaEventDestroy(c->ev[i]);
   delete c;
+}
+
+// Linear textures over the padded factor buffers (16-byte texels: float4 or
+// two doubles as int4); a factor wider than the device's linear texture limit
+// keeps texture 0 and is gathered with plain loads.
+void make_factor_tex(tucker_ctx* c, int m) {
+  int dev = 0, maxw = 0;
+  TK_CUDA(cudaGetDevice(&dev));
+  TK_CUDA(cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxTexture1DLinearWidth, dev));
+  const size_t bytes = (size_t)c->L[m] * c->ldF[m] * c->esz;
+  if (bytes / 16 > (size_t)maxw || bytes / 16 > (size_t)INT32_MAX) return;
+  for (int w = 0; w < 2; ++w) {
+    cudaResourceDesc rd{};
+    rd.resType = cudaResourceTypeLinear;
+    rd.res.linear.devPtr = w ? c->Fb[m] : c->Fa[m];
+    rd.res.linear.desc = c->prec == TUCKER_FP32 ? cudaCreateChannelDesc<float4>() : cudaCreateChannelDesc<int4>();
+    rd.res.linear.sizeInBytes = bytes;
+    cudaTextureDesc td{};
+    td.readMode = cudaReadModeElementType;
+    TK_CUDA(cudaCreateTextureObject(w ? &c->texFb[m] : &c->texFa[m], &rd, &td, nullptr));
+  }
 }
 
 void copy_in_factors(tucker_ctx* c, const void* const* d_F, int skip, cudaStream_t s) {
@@ -267,6 +292,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
       c->Fb[m] = tk_alloc(c, (size_t)L[m] * c->ldF[m] * esz);
       TK_CUDA(cudaMemsetAsync(c->Fa[m], 0, (size_t)L[m] * c->ldF[m] * esz, s));
       TK_CUDA(cudaMemsetAsync(c->Fb[m], 0, (size_t)L[m] * c->ldF[m] * esz, s));
+      make_factor_tex(c, m);
     }
     TK_CUDA(cudaStreamSynchronize(s));
     *out = c;
@@ -404,3 +430,11 @@ tucker_status tucker_memory(tucker_t t, int64_t* bytes) {
 }
 
 }  // extern "C"
+
+cudaTextureObject_t tk_factor_tex(const tucker_ctx* c, const void* F) {
+  for (int m = 0; m < c->N; ++m) {
+    if (F == c->Fa[m]) return c->texFa[m];
+    if (F == c->Fb[m]) return c->texFb[m];
+  }
+  return 0;
+}

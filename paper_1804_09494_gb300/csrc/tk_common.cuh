@@ -110,6 +110,10 @@ struct tucker_ctx {
   int ldF[TK_MAXN] = {};
   void* Fa[TK_MAXN] = {};   // current factors
   void* Fb[TK_MAXN] = {};   // new factors
+  // linear textures over Fa / Fb (one texel = 16 bytes; 0 where the factor
+  // exceeds the device's linear texture width)
+  cudaTextureObject_t texFa[TK_MAXN] = {};
+  cudaTextureObject_t texFb[TK_MAXN] = {};
   // workspace
   void* Z = nullptr;        // max_n R_n * Khat_n
   void* Zpart = nullptr;    // max_n 2 * P_n * Khat_n
@@ -180,6 +184,8 @@ void tk_alloc_fuws(tucker_ctx* c, int n);
 
 // ---- core / fit (tk_core.cu) ----
 void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s);
+// texture object over one of the context's factor buffers (0 if none)
+cudaTextureObject_t tk_factor_tex(const tucker_ctx* c, const void* F);
 double tk_norm2(tucker_ctx* c, const void* vals, int64_t n, cudaStream_t s);
 
 // ---- small device utilities ----

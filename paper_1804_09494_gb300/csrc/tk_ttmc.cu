@@ -11,9 +11,15 @@
 // block j0 of b, are fixed per column group g.  A whole slice is written to its
 // compact Z row once; a split piece goes to a per-bin partial slot and the
 // fix-up adds the pieces in bin order (deterministic, FP64 sums).
+//
+// The kernel is bound by the latency of the two row gathers per element: the
+// F_a row is read through the LSU path and the F_b block through the texture
+// path (two L1 pipelines), and the element stream and the Z rows carry an L2
+// evict-first policy so that the reused factor rows stay in L2.
 #include <algorithm>
 
 #include "tk_common.cuh"
+
 
 namespace {
 
@@ -39,6 +45,7 @@ struct TtmcArgs {
   const int32_t* bin_len;
   const T* vals_override;
   const T* F[TK_MAXN - 1];  // factors of the other modes, increasing mode order
+  cudaTextureObject_t texB; // texture over the second remaining factor (0: plain loads)
   int ld[TK_MAXN - 1];      // their (padded) leading dimensions
   int Kf[TK_MAXN - 1];
   int nother;
@@ -94,14 +101,58 @@ __device__ __forceinline__ void load_row(const T* __restrict__ row, int valid, T
   }
 }
 
+// The same through the texture path (texel = one 16-byte vector), so that the
+// two gathered rows of an element use the LSU and the texture pipelines.
+__device__ __forceinline__ void tex_vec(cudaTextureObject_t t, int i, float* o) {
+  unpack(tex1Dfetch<float4>(t, i), o);
+}
+__device__ __forceinline__ void tex_vec(cudaTextureObject_t t, int i, double* o) {
+  const int4 v = tex1Dfetch<int4>(t, i);
+  o[0] = __hiloint2double(v.y, v.x);
+  o[1] = __hiloint2double(v.w, v.z);
+}
+template <typename T, int M>
+__device__ __forceinline__ void tex_row(cudaTextureObject_t t, int64_t first, int valid, T (&out)[Row<T, M>::R]) {
+  constexpr int W = VecT<T>::W;
+#pragma unroll
+  for (int v = 0; v < Row<T, M>::NV; ++v) {
+    if (v * W < valid) {
+      tex_vec(t, (int)(first / W) + v, &out[v * W]);
+    } else {
+#pragma unroll
+      for (int u = 0; u < W; ++u) out[v * W + u] = T(0);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- staging
 // Each warp streams the element arrays of its 32 bins through shared memory:
 // steps [k0, k0+C) of a warp occupy one contiguous span per array (the
 // warp-interleaved layout), copied with 16-byte cp.async into one of two
 // buffers while the other buffer is being consumed.
+// The element stream and the Z rows are touched once per launch: they are
+// marked evict-first in L2 so that they do not displace the factor rows, which
+// are gathered again and again.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc),
+               "l"(l2_evict_first())
+               : "memory");
+}
+__device__ __forceinline__ void st_stream(float4* p, const float4& v) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(l2_evict_first())
+               : "memory");
+}
+__device__ __forceinline__ void st_stream(double2* p, const double2& v) {
+  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y),
+               "l"(l2_evict_first())
+               : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
@@ -179,7 +230,7 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
       using V = typename VecT<T>::type;
       V* d = reinterpret_cast<V*>(dst);
 #pragma unroll
-      for (int v = 0; v < MA * MB / VecT<T>::W; ++v) d[v] = pack(&acc[v * VecT<T>::W]);
+      for (int v = 0; v < MA * MB / VecT<T>::W; ++v) st_stream(d + v, pack(&acc[v * VecT<T>::W]));
     } else {
 #pragma unroll
       for (int jj = 0; jj < MB; ++jj)
@@ -195,41 +246,48 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
   if (nch > 1) issue_chunk(a, wsm + sb, CW, wbase, C, min(C, wlen - C), lane, sval, sperm);
   cp_commit();
   uint32_t cur = len > 0 ? a.rowcode[wbase * 32 + lane] : 0u;
+  // gathers element sj's rows and its outer-mode scaling into v, fa, fb
+  auto gather = [&](const uint32_t* sw, int CW_, int sj, T& v, T (&fa)[Row<T, MA>::R], T (&fb)[Row<T, MB>::R]) {
+    for (int q = 2; q < a.nother; ++q) v *= __ldg(a.F[q] + (int64_t)(int32_t)sw[(1 + q) * CW_ + sj] * a.ld[q] + oc[q - 2]);
+    load_row<T, MA>(a.F[0] + (int64_t)(int32_t)sw[CW_ + sj] * a.ld[0], ka, fa);
+    if (a.nother >= 2) {
+      const int64_t rb = (int64_t)(int32_t)sw[2 * CW_ + sj] * a.ld[1] + j0;
+      if (a.texB) tex_row<T, MB>(a.texB, rb, tb, fb);
+      else load_row<T, MB>(a.F[1] + rb, tb, fb);
+    } else {
+#pragma unroll
+      for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
+    }
+  };
+  auto accumulate = [&](uint32_t code, T v, const T (&fa)[Row<T, MA>::R], const T (&fb)[Row<T, MB>::R]) {
+    if (code != cur) {
+      flush(cur);
+#pragma unroll
+      for (int i = 0; i < MA * MB; ++i) acc[i] = T(0);
+      cur = code;
+    }
+#pragma unroll
+    for (int jj = 0; jj < MB; ++jj) {
+      const T t = v * fb[jj];
+#pragma unroll
+      for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(fa[i], t, acc[i + MA * jj]);
+    }
+  };
   for (int c = 0; c < nch; ++c) {
     cp_wait_1();
     __syncwarp();
     const uint32_t* sw = (const uint32_t*)(wsm + (c & 1) * sb);
     const T* sv = (const T*)(sw + (1 + a.nother) * CW);
     const int32_t* sp = (const int32_t*)((const char*)sv + (sval ? (size_t)CW * sizeof(T) : 0));
-    const int ns = min(C, wlen - c * C);
+    // this lane's steps in the chunk
+    const int ns = min(C, len - c * C);
 #pragma unroll 1
     for (int j = 0; j < ns; ++j) {
-      if (c * C + j >= len) break;
       const int sj = j * 32 + lane;
-      const uint32_t code = sw[sj];
-      if (code != cur) {
-        flush(cur);
-#pragma unroll
-        for (int i = 0; i < MA * MB; ++i) acc[i] = T(0);
-        cur = code;
-      }
       T v = sval ? sv[sj] : a.vals_override[sp[sj]];
-      for (int q = 2; q < a.nother; ++q) v *= __ldg(a.F[q] + (int64_t)(int32_t)sw[(1 + q) * CW + sj] * a.ld[q] + oc[q - 2]);
-      T fa[Row<T, MA>::R];
-      load_row<T, MA>(a.F[0] + (int64_t)(int32_t)sw[CW + sj] * a.ld[0], ka, fa);
-      T fb[Row<T, MB>::R];
-      if (a.nother >= 2) {
-        load_row<T, MB>(a.F[1] + (int64_t)(int32_t)sw[2 * CW + sj] * a.ld[1] + j0, tb, fb);
-      } else {
-#pragma unroll
-        for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
-      }
-#pragma unroll
-      for (int jj = 0; jj < MB; ++jj) {
-        const T t = v * fb[jj];
-#pragma unroll
-        for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(fa[i], t, acc[i + MA * jj]);
-      }
+      T fa[Row<T, MA>::R], fb[Row<T, MB>::R];
+      gather(sw, CW, sj, v, fa, fb);
+      accumulate(sw[sj], v, fa, fb);
     }
     __syncwarp();
     if (c + 2 < nch) issue_chunk(a, wsm + (c & 1) * sb, CW, wbase, (c + 2) * C, min(C, wlen - (c + 2) * C), lane, sval, sperm);
@@ -502,7 +560,8 @@ Plan make_plan(const tucker_ctx* c, int n) {
   for (int i = 0; i < kNumTiles; ++i) {
     const Tile& t = tiles[i];
     const bool okA = t.EA ? p.KA == t.MA : p.KA <= t.MA;
-    const bool okB = t.EB ? (p.KB % t.MB == 0) : true;
+    // an exact b block must start on a vector boundary of the padded rows
+    const bool okB = t.EB ? (p.KB % t.MB == 0 && (p.KB == t.MB || t.MB % (16 / c->esz) == 0)) : true;
     if (okA && okB) {
       p.tile_id = i;
       p.tile = t;
@@ -570,6 +629,7 @@ void forward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const vo
   a.Zpart = (T*)c->Zpart;
   a.store_vec = ((uintptr_t)Z % 16 == 0) && (md.Khat % VecT<T>::W == 0) &&
                 ((pl.KA * pl.tile.MB) % VecT<T>::W == 0);
+  a.texB = pl.nother >= 2 ? tk_factor_tex(c, F[pl.others[1]]) : 0;
   a.chunk = stage_chunk<T>(pl.nother);
   const int shm = 4 * 2 * stage_bytes<T>(a.chunk, pl.nother, vals_override == nullptr, vals_override != nullptr);
   set_smem_attr(fwd_kernel<T>(pl.tile_id), shm);
