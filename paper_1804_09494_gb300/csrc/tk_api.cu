@@ -241,7 +241,9 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
       int P = o.P_bins;
       if (P == 0) {
         const int64_t tpsm = tk_ttmc_threads_per_sm(c, n);
-        int64_t p = (int64_t)c->sm_count * tpsm / G;
+        // one CTA slot short of a full wave, so that a one-CTA kernel of a
+        // concurrent factor update finds room beside the TTM-chain
+        int64_t p = ((int64_t)c->sm_count * tpsm - 128) / G;
         p = std::min<int64_t>(p, tk_ceil_div(tk_ceil_div(nnz, 16), 32) * 32);
         p = std::max<int64_t>(32, p / 32 * 32);
         P = (int)p;
@@ -277,6 +279,10 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
       TK_CUDA(cudaStreamCreateWithFlags(&c->aux[n], cudaStreamNonBlocking));
       TK_CUDA(cudaEventCreateWithFlags(&c->ev_ttm[n], cudaEventDisableTiming));
       TK_CUDA(cudaEventCreateWithFlags(&c->ev_fu[n], cudaEventDisableTiming));
+    }
+    {
+      const tk_mode& mc = c->mode[tk_core_mode(c)];
+      c->Zcore = tk_alloc(c, (size_t)std::max(mc.R, 1) * mc.Khat * esz);
     }
     (void)zc;
     (void)wp;
@@ -373,17 +379,23 @@ tucker_status hooi_iter(tucker_t t, void* const* d_F, void* d_G, double* h_fit, 
     } else {
       // Fig. 1 as printed: every TTM-chain reads the input factors, so the
       // factor update of mode n (side stream n) overlaps the TTM-chains of the
-      // later modes on the caller's stream.
-      for (int n = 0; n < t->N; ++n) {
+      // later modes on the caller's stream.  The mode whose TTM-chain forms the
+      // core goes last: its factor update overlaps that TTM-chain, which does
+      // not read it.
+      const int nc = tk_core_mode(t);
+      for (int i = 0; i < t->N; ++i) {
+        const int n = i < t->N - 1 ? (i < nc ? i : i + 1) : nc;
         tk_ttmc_forward(t, n, t->Fa, t->ldF, nullptr, t->Zm[n], s);
         TK_CUDA(cudaEventRecord(t->ev_ttm[n], s));
         TK_CUDA(cudaStreamWaitEvent(t->aux[n], t->ev_ttm[n], 0));
         tk_factor_update(t, n, t->Zm[n], t->Fb[n], t->ldF[n], nullptr, t->aux[n]);
         TK_CUDA(cudaEventRecord(t->ev_fu[n], t->aux[n]));
       }
-      for (int n = 0; n < t->N; ++n) TK_CUDA(cudaStreamWaitEvent(s, t->ev_fu[n], 0));
+      for (int n = 0; n < t->N; ++n)
+        if (n != nc) TK_CUDA(cudaStreamWaitEvent(s, t->ev_fu[n], 0));
+      tk_core(t, t->Fb, t->ldF, d_G, s, t->ev_fu[nc]);
     }
-    tk_core(t, t->Fb, t->ldF, d_G, s);
+    if (t->gauss_seidel) tk_core(t, t->Fb, t->ldF, d_G, s);
     for (int m = 0; m < t->N; ++m) tk_copy_factor(t, t->Fb[m], t->ldF[m], d_F[m], t->K[m], t->L[m], t->K[m], s);
     if (h_fit) {
       TK_CUDA(cudaMemcpyAsync(h_fit, t->fit_d + 1, sizeof(double), cudaMemcpyDeviceToHost, s));

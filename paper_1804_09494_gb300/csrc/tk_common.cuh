@@ -120,6 +120,8 @@ struct tucker_ctx {
   double* Zchunk = nullptr; // max_n nchunks * Khat_n
   tk_fuws fu[TK_MAXN];      // factor-update workspace, one per mode (modes overlap on side streams)
   void* Zm[TK_MAXN] = {};   // per-mode penultimate matrices (R_n x Khat_n)
+  void* Zcore = nullptr;    // the core's penultimate matrix (mode tk_core_mode), apart from
+                            // Zm so that it can be formed while that mode's update reads Zm
   cudaStream_t aux[TK_MAXN] = {};
   cudaEvent_t ev_ttm[TK_MAXN] = {};
   cudaEvent_t ev_fu[TK_MAXN] = {};
@@ -183,7 +185,10 @@ void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_
 void tk_alloc_fuws(tucker_ctx* c, int n);
 
 // ---- core / fit (tk_core.cu) ----
-void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s);
+// New core from the TTM-chain of mode tk_core_mode(c); with before_Fn, the
+// stream waits on that event after the TTM-chain, before F_n is first read.
+int tk_core_mode(const tucker_ctx* c);
+void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s, cudaEvent_t before_Fn = nullptr);
 // texture object over one of the context's factor buffers (0 if none)
 cudaTextureObject_t tk_factor_tex(const tucker_ctx* c, const void* F);
 double tk_norm2(tucker_ctx* c, const void* vals, int64_t n, cudaStream_t s);

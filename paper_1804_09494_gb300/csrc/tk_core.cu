@@ -131,24 +131,19 @@ __global__ void k_sum_final(const double* part, int n, double* out) {
 }
 
 template <typename T>
-void core_impl(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s) {
-  // the mode with the smallest TTM-chain work (nnz * Khat) and then the fewest rows
-  int best = 0;
-  for (int n = 1; n < c->N; ++n) {
-    const tk_mode& a = c->mode[n];
-    const tk_mode& b = c->mode[best];
-    if (a.Khat < b.Khat || (a.Khat == b.Khat && a.R < b.R)) best = n;
-  }
-  const int n = best;
+void core_impl(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s, cudaEvent_t before_Fn) {
+  const int n = tk_core_mode(c);
   const tk_mode& md = c->mode[n];
-  tk_ttmc_forward(c, n, F, ldF, nullptr, c->Zm[n], s);
+  // the TTM-chain of mode n does not read F_n: the producer of F_n may still run
+  tk_ttmc_forward(c, n, F, ldF, nullptr, c->Zcore, s);
+  if (before_Fn) TK_CUDA(cudaStreamWaitEvent(s, before_Fn, 0));
   tk_phase_begin(c, PH_CORE, s);
   const int K = c->K[n], Khat = md.Khat, R = md.R;
   const int cb = (int)tk_ceil_div(Khat, 128);
   int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), tk_ceil_div(4 * c->sm_count, cb)));
   const int rps = (int)tk_ceil_div(R, nsplit);
   dim3 grid(cb, nsplit);
-  const T* Z = (const T*)c->Zm[n];
+  const T* Z = (const T*)c->Zcore;
   const T* Fn = (const T*)F[n];
   if (K <= 8) k_core_partial<T, 8><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
   else if (K <= 16) k_core_partial<T, 16><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
@@ -168,9 +163,20 @@ void core_impl(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaS
 
 }  // namespace
 
-void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s) {
-  if (c->prec == TUCKER_FP32) core_impl<float>(c, F, ldF, G_out, s);
-  else core_impl<double>(c, F, ldF, G_out, s);
+// the mode with the smallest TTM-chain work (nnz * Khat) and then the fewest rows
+int tk_core_mode(const tucker_ctx* c) {
+  int best = 0;
+  for (int n = 1; n < c->N; ++n) {
+    const tk_mode& a = c->mode[n];
+    const tk_mode& b = c->mode[best];
+    if (a.Khat < b.Khat || (a.Khat == b.Khat && a.R < b.R)) best = n;
+  }
+  return best;
+}
+
+void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStream_t s, cudaEvent_t before_Fn) {
+  if (c->prec == TUCKER_FP32) core_impl<float>(c, F, ldF, G_out, s, before_Fn);
+  else core_impl<double>(c, F, ldF, G_out, s, before_Fn);
 }
 
 double tk_norm2(tucker_ctx* c, const void* vals, int64_t n, cudaStream_t s) {

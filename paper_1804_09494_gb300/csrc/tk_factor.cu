@@ -339,7 +339,6 @@ template <typename T>
 __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ T red[33];
-  __shared__ double redd[33];
   __shared__ double lo_s[TK_MAXK], hi_s[TK_MAXK];
   __shared__ T lam_s[TK_MAXK], inv_sig[TK_MAXK];
   __shared__ double C[TK_MAXK][TK_MAXK + 1];
@@ -634,6 +633,374 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   }
   __syncthreads();
   for (int idx = tid; idx < n * K; idx += nt) a.Vs[idx] = (T)a.Vout[idx] * inv_sig[idx % K];
+  if (a.clk && tid == 0) a.clk[7] = clock64();
+}
+
+// Compact form of the same eigensolver for Gram matrices that fit in shared
+// memory with their Lanczos basis (Khat up to about 150 in FP32): 128 threads,
+// thread r owning rows r, r + 128 of every Lanczos vector, so that a step needs
+// no cross-warp shuffles -- only seven short barriers:
+//   w = A q_j           thread r: dot of column-major A's row r with q_j
+//   h = Q^T w, w -= Q h thread k forms h_k, thread r its row of Q h (twice)
+//   beta = ||w||        block sum
+// Q is stored row-major with an odd leading dimension (ldq), conflict-free for
+// both the per-k and the per-r sweeps.  The tridiagonal phases and the modified
+// Gram-Schmidt of the eigenvectors work in shared memory; the FP64 refinement
+// is the same as in k_eig.
+constexpr int kEigSmallThreads = 128;
+
+template <typename T>
+__host__ __device__ inline int eig_small_ldq(int n) {
+  return n | 1;
+}
+// dynamic shared memory: A (n*n; reused for the inverse-iteration factors when
+// 6*K*n <= n*n), Q (n*ldq), X (n*K), 6 vectors of n, the factors (if not reused)
+// (after two K x (K+1) FP64 matrices for the refinement's Cholesky factor)
+template <typename T>
+__host__ __device__ inline size_t eig_small_smem(int n, int K) {
+  const size_t tri = (size_t)6 * K * n;
+  size_t e = (size_t)n * n + (size_t)n * eig_small_ldq<T>(n) + (size_t)n * K + (size_t)6 * n;
+  if (tri > (size_t)n * n) e += tri;
+  return (size_t)2 * K * (K + 1) * sizeof(double) + e * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ T red[33];
+  __shared__ double lo_s[TK_MAXK], hi_s[TK_MAXK];
+  __shared__ T lam_s[TK_MAXK], inv_sig[TK_MAXK];
+  __shared__ int cnt_s[kEigSmallThreads];
+  __shared__ T mn_s[4], mx_s[4], b2_s[4];
+  const int n = a.n, K = a.K, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NT = kEigSmallThreads, NW = NT / 32;
+  const int m = n, ldq = eig_small_ldq<T>(n);
+  // Cholesky factor C and its inverse Ri (refinement), K x (K + 1) row-major
+  double* Cm = (double*)smem;
+  double* Rm = Cm + K * (K + 1);
+  T* A = (T*)(Rm + K * (K + 1));
+  T* Q = A + (size_t)n * n;
+  T* Xs = Q + (size_t)n * ldq;
+  T* ws = Xs + (size_t)n * K;
+  T* hs = ws + n;
+  T* ta = hs + n;
+  T* tb = ta + n;
+  T* tb2 = tb + n;
+  T* tri = ((size_t)6 * K * n <= (size_t)n * n) ? A : tb2 + n;
+
+  T fro2 = T(0);
+  for (int idx = tid; idx < n * n; idx += NT) {
+    const T v = (T)a.W[idx];  // W symmetric: row-major = column-major
+    A[idx] = v;
+    fro2 = fma(v, v, fro2);
+  }
+  const T fro = sqrt(block_sum<T>(fro2, red));
+  const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16);
+  if (a.clk && tid == 0) a.clk[0] = clock64();
+
+  // rows owned by this thread (n <= 2 * NT)
+  const int r0 = tid, r1 = tid + NT;
+  const bool h0 = r0 < n, h1 = r1 < n;
+  T w0 = T(0), w1 = T(0);
+  // start vector
+  {
+    if (h0) w0 = hash_unit<T>(1, r0);
+    if (h1) w1 = hash_unit<T>(1, r1);
+    const T inv = T(1) / sqrt(block_sum<T>(w0 * w0 + w1 * w1, red));
+    if (h0) Q[(size_t)r0 * ldq] = w0 * inv;
+    if (h1) Q[(size_t)r1 * ldq] = w1 * inv;
+    __syncthreads();
+  }
+  // one classical Gram-Schmidt pass of (w0, w1) against q_0..q_j; returns h_j
+  auto cgs = [&](int j) -> T {
+    if (h0) ws[r0] = w0;
+    if (h1) ws[r1] = w1;
+    __syncthreads();
+    for (int k = tid; k <= j; k += NT) {
+      T s0 = T(0), s1 = T(0);
+      int r = 0;
+      for (; r + 1 < n; r += 2) {
+        s0 = fma(Q[(size_t)r * ldq + k], ws[r], s0);
+        s1 = fma(Q[(size_t)(r + 1) * ldq + k], ws[r + 1], s1);
+      }
+      if (r < n) s0 = fma(Q[(size_t)r * ldq + k], ws[r], s0);
+      hs[k] = s0 + s1;
+    }
+    __syncthreads();
+    if (h0) {
+      const T* qr = Q + (size_t)r0 * ldq;
+      T s0 = T(0), s1 = T(0);
+      int k = 0;
+      for (; k + 1 <= j; k += 2) {
+        s0 = fma(qr[k], hs[k], s0);
+        s1 = fma(qr[k + 1], hs[k + 1], s1);
+      }
+      if (k <= j) s0 = fma(qr[k], hs[k], s0);
+      w0 -= s0 + s1;
+    }
+    if (h1) {
+      const T* qr = Q + (size_t)r1 * ldq;
+      T s0 = T(0), s1 = T(0);
+      int k = 0;
+      for (; k + 1 <= j; k += 2) {
+        s0 = fma(qr[k], hs[k], s0);
+        s1 = fma(qr[k + 1], hs[k + 1], s1);
+      }
+      if (k <= j) s0 = fma(qr[k], hs[k], s0);
+      w1 -= s0 + s1;
+    }
+    return hs[j];
+  };
+
+  for (int j = 0; j < m; ++j) {
+    // w = A q_j
+    {
+      T s0 = T(0), s1 = T(0), u0 = T(0), u1 = T(0);
+      int cc = 0;
+      for (; cc + 1 < n; cc += 2) {
+        const T q0 = Q[(size_t)cc * ldq + j], q1 = Q[(size_t)(cc + 1) * ldq + j];
+        if (h0) {
+          s0 = fma(A[(size_t)cc * n + r0], q0, s0);
+          s1 = fma(A[(size_t)(cc + 1) * n + r0], q1, s1);
+        }
+        if (h1) {
+          u0 = fma(A[(size_t)cc * n + r1], q0, u0);
+          u1 = fma(A[(size_t)(cc + 1) * n + r1], q1, u1);
+        }
+      }
+      if (cc < n) {
+        const T q0 = Q[(size_t)cc * ldq + j];
+        if (h0) s0 = fma(A[(size_t)cc * n + r0], q0, s0);
+        if (h1) u0 = fma(A[(size_t)cc * n + r1], q0, u0);
+      }
+      w0 = s0 + s1;
+      w1 = u0 + u1;
+    }
+    T al = cgs(j);
+    __syncthreads();  // hs is rewritten by the second pass
+    al += cgs(j);
+    if (tid == 0) ta[j] = al;
+    const T bnorm = sqrt(block_sum<T>(w0 * w0 + w1 * w1, red));
+    if (j == m - 1) break;
+    if (bnorm > T(100) * eps * fro) {
+      if (tid == 0) tb[j] = bnorm;
+      const T inv = T(1) / bnorm;
+      if (h0) Q[(size_t)r0 * ldq + j + 1] = w0 * inv;
+      if (h1) Q[(size_t)r1 * ldq + j + 1] = w1 * inv;
+    } else {
+      // invariant subspace: continue with a fresh vector orthogonal to q_0..q_j
+      if (tid == 0) tb[j] = T(0);
+      w0 = h0 ? hash_unit<T>(j + 2, r0) : T(0);
+      w1 = h1 ? hash_unit<T>(j + 2, r1) : T(0);
+      cgs(j);
+      __syncthreads();
+      cgs(j);
+      const T n2 = block_sum<T>(w0 * w0 + w1 * w1, red);
+      const T inv = n2 > T(0) ? T(1) / sqrt(n2) : T(0);
+      if (h0) Q[(size_t)r0 * ldq + j + 1] = w0 * inv;
+      if (h1) Q[(size_t)r1 * ldq + j + 1] = w1 * inv;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) tb[m - 1] = T(0);
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[1] = clock64();
+
+  // ---- Gershgorin interval and pivot threshold
+  {
+    T mn = T(INFINITY), mx = T(-INFINITY), b2m = T(0);
+    for (int i = tid; i < m; i += NT) {
+      const T bb = tb[i];
+      tb2[i] = bb * bb;
+      const T r = (i > 0 ? fabs(tb[i - 1]) : T(0)) + fabs(bb);
+      mn = fmin(mn, ta[i] - r);
+      mx = fmax(mx, ta[i] + r);
+      b2m = fmax(b2m, bb * bb);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      b2m = fmax(b2m, __shfl_xor_sync(0xffffffffu, b2m, o));
+    }
+    if (lane == 0) {
+      mn_s[wid] = mn;
+      mx_s[wid] = mx;
+      b2_s[wid] = b2m;
+    }
+    __syncthreads();
+    if (tid < K) {
+      T lo = T(INFINITY), hi = T(-INFINITY);
+      for (int i = 0; i < NW; ++i) {
+        lo = fmin(lo, mn_s[i]);
+        hi = fmax(hi, mx_s[i]);
+      }
+      const T pad = T(1e-6) * (hi - lo) + T(10) * eps * fabs(hi) + T(1e-30);
+      lo_s[tid] = (double)(lo - pad);
+      hi_s[tid] = (double)(hi + pad);
+    }
+    if (tid == 0) {
+      T b2 = T(0);
+      for (int i = 0; i < NW; ++i) b2 = fmax(b2, b2_s[i]);
+      red[0] = (sizeof(T) == 4 ? T(1e-30) : T(1e-290)) * fmax(T(1), b2);
+    }
+    __syncthreads();
+  }
+  const T pivmin = red[0];
+  __syncthreads();
+  // ---- multisection for the K largest eigenvalues of T (NT / K sections each)
+  {
+    const int S = NT / K;
+    const double inv_s1 = 1.0 / (double)(S + 1);
+    // shrink by (S + 1) per round down to FP rounding of the interval width
+    const int rounds = (int)ceil((sizeof(T) == 4 ? 24.0 : 53.0) * 0.6931471805599453 / log((double)(S + 1))) + 1;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int k = tid / S, sidx = tid - k * S;
+      if (k < K) {
+        const double step = (hi_s[k] - lo_s[k]) * inv_s1;
+        cnt_s[tid] = sturm_count<T>(ta, tb2, m, (T)(lo_s[k] + step * (double)(sidx + 1)), pivmin);
+      }
+      __syncthreads();
+      if (tid < K) {
+        const int target = m - 1 - tid;  // ascending index of the (tid+1)-th largest eigenvalue
+        const double l0 = lo_s[tid], step = (hi_s[tid] - l0) * inv_s1;
+        double nlo = l0, nhi = hi_s[tid];
+        for (int s2 = 0; s2 < S; ++s2) {
+          if (cnt_s[tid * S + s2] <= target) {
+            nlo = l0 + step * (double)(s2 + 1);
+          } else {
+            nhi = l0 + step * (double)(s2 + 1);
+            break;
+          }
+        }
+        lo_s[tid] = nlo;
+        hi_s[tid] = nhi;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid < K) lam_s[tid] = (T)(0.5 * (lo_s[tid] + hi_s[tid]));
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[2] = clock64();
+  // ---- inverse iteration, one thread per eigenvalue, factors in shared memory
+  for (int k = tid; k < K; k += NT) {
+    T* lu = tri + (size_t)k * 6 * m;
+    T* x = lu + 5 * m;
+    const T tiny = eps * fro + T(1e-30);
+    tri_factor<T>(ta, tb, m, lam_s[k], tiny, lu);
+    for (int i = 0; i < m; ++i) x[i] = hash_unit<T>(101 + k, i);
+    for (int it = 0; it < 3; ++it) {
+      tri_solve<T>(lu, m, x);
+      T nn = T(0);
+      for (int i = 0; i < m; ++i) nn = fma(x[i], x[i], nn);
+      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
+      for (int i = 0; i < m; ++i) x[i] *= inv;
+    }
+  }
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[3] = clock64();
+  // ---- X = Q S (row r of X from row r of Q)
+  for (int idx = tid; idx < n * K; idx += NT) {
+    const int r = idx / K, k = idx - r * K;
+    const T* x = tri + (size_t)k * 6 * m + 5 * m;
+    const T* qr = Q + (size_t)r * ldq;
+    T s0 = T(0), s1 = T(0);
+    int j = 0;
+    for (; j + 1 < m; j += 2) {
+      s0 = fma(qr[j], x[j], s0);
+      s1 = fma(qr[j + 1], x[j + 1], s1);
+    }
+    if (j < m) s0 = fma(qr[j], x[j], s0);
+    Xs[idx] = s0 + s1;
+  }
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[4] = clock64();
+  // ---- modified Gram-Schmidt on one warp (separates clustered eigenvalues)
+  if (wid == 0) {
+    for (int k = 0; k < K; ++k) {
+      for (int j = 0; j < k; ++j) {
+        T d = T(0);
+        for (int r = lane; r < n; r += 32) d = fma(Xs[r * K + j], Xs[r * K + k], d);
+        d = warp_allsum(d);
+        for (int r = lane; r < n; r += 32) Xs[r * K + k] -= d * Xs[r * K + j];
+        __syncwarp();
+      }
+      T nn = T(0);
+      for (int r = lane; r < n; r += 32) nn = fma(Xs[r * K + k], Xs[r * K + k], nn);
+      nn = warp_allsum(nn);
+      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
+      for (int r = lane; r < n; r += 32) Xs[r * K + k] *= inv;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[5] = clock64();
+  if (a.polish) {
+    // FP64 refinement: Y = W X, C = Y^T Y, C = R^T R, X' = Y R^-1, sigma_k^2 ~ R_kk
+    for (int idx = tid; idx < n * K; idx += NT) {
+      const int i = idx / K, k = idx - i * K;
+      double s2 = 0.0;
+      const double* wr = a.W + (int64_t)i * n;
+      for (int cc = 0; cc < n; ++cc) s2 = fma(wr[cc], (double)Xs[cc * K + k], s2);
+      a.Y[idx] = s2;
+    }
+    __syncthreads();
+    if (a.clk && tid == 0) a.clk[6] = clock64();
+    for (int pr = tid; pr < K * K; pr += NT) {
+      const int r = pr / K, cc = pr - r * K;
+      if (r <= cc) {
+        double s2 = 0.0;
+        for (int i = 0; i < n; ++i) s2 = fma(a.Y[i * K + r], a.Y[i * K + cc], s2);
+        Cm[(r) * (K + 1) + (cc)] = s2;
+        Cm[(cc) * (K + 1) + (r)] = s2;
+      }
+    }
+    __syncthreads();
+    if (wid == 0) {  // Cholesky C = L L^T (lower, in place) and Ri = L^-T (upper), one warp
+      bool bad = false;
+      for (int j = 0; j < K; ++j) {
+        double d = Cm[(j) * (K + 1) + (j)];
+        if (!(d > 0.0)) bad = true;
+        d = d > 0.0 ? sqrt(d) : 1.0;
+        __syncwarp();
+        if (lane == j) Cm[(j) * (K + 1) + (j)] = d;
+        if (lane > j && lane < K) Cm[(lane) * (K + 1) + (j)] /= d;
+        __syncwarp();
+        if (lane > j && lane < K)
+          for (int k2 = j + 1; k2 <= lane; ++k2) Cm[(lane) * (K + 1) + (k2)] -= Cm[(lane) * (K + 1) + (j)] * Cm[(k2) * (K + 1) + (j)];
+        __syncwarp();
+      }
+      if (bad && lane == 0) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
+      if (lane < K) {
+        for (int i = K - 1; i >= 0; --i) {
+          double s2 = (i == lane) ? 1.0 : 0.0;
+          for (int k2 = i + 1; k2 < K; ++k2) s2 -= Cm[(k2) * (K + 1) + (i)] * Rm[(k2) * (K + 1) + (lane)];
+          Rm[(i) * (K + 1) + (lane)] = (i <= lane) ? s2 / Cm[(i) * (K + 1) + (i)] : 0.0;
+        }
+        a.sigma[lane] = sqrt(fabs(Cm[(lane) * (K + 1) + (lane)]));
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * K; idx += NT) {
+      const int i = idx / K, k = idx - i * K;
+      double s2 = 0.0;
+      for (int j = 0; j <= k; ++j) s2 = fma(a.Y[i * K + j], Rm[(j) * (K + 1) + (k)], s2);
+      a.Vout[idx] = s2;
+    }
+  } else {
+    for (int idx = tid; idx < n * K; idx += NT) a.Vout[idx] = (double)Xs[idx];
+    for (int k = tid; k < K; k += NT) a.sigma[k] = sqrt(fmax((double)lam_s[k], 0.0));
+  }
+  __syncthreads();
+  if (tid < K) {
+    const double sg = a.sigma[tid];
+    const bool ok = sg > 0.0 && isfinite(sg);
+    if (!ok) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
+    inv_sig[tid] = ok ? (T)(1.0 / sg) : T(0);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * K; idx += NT) a.Vs[idx] = (T)a.Vout[idx] * inv_sig[idx % K];
   if (a.clk && tid == 0) a.clk[7] = clock64();
 }
 
@@ -1056,11 +1423,14 @@ void set_tile_attr(Kern k, size_t bytes) {
   TK_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)std::max<size_t>(bytes, 48 * 1024)));
 }
 
+constexpr size_t kEigSmallSmemMax = 200 * 1024;
+
 template <typename T>
 void setup_eig_attr() {
   static bool done = false;
   if (!done) {
     TK_CUDA(cudaFuncSetAttribute(k_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    TK_CUDA(cudaFuncSetAttribute(k_eig_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmallSmemMax));
     done = true;
   }
 }
@@ -1129,6 +1499,8 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     const size_t work = (size_t)5 * Khat * sizeof(T) + 64;
     a.use_smem = (mat + work) <= 150 * 1024;
     const size_t shm = (a.use_smem ? mat : 0) + work;
+    const size_t shm_small = eig_small_smem<T>(Khat, K);
+    const bool small = Khat <= 2 * kEigSmallThreads && shm_small <= kEigSmallSmemMax;
     a.polish = c->prec == TUCKER_FP32;
     a.X = ws->eigX;
     a.Y = ws->eigX + (size_t)Khat * K;
@@ -1138,7 +1510,8 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     a.sigma = ws->sigma;
     a.Vs = (T*)ws->Vs;
     a.err = c->err;
-    k_eig<T><<<1, 1024, shm, s>>>(a);
+    if (small) k_eig_small<T><<<1, kEigSmallThreads, shm_small, s>>>(a);
+    else k_eig<T><<<1, 1024, shm, s>>>(a);
     TK_CUDA(cudaGetLastError());
     tk_launched(c, PH_EIG);
   }
