@@ -177,7 +177,9 @@ void tk_ttmc_backward(tucker_ctx* c, int n, void* const* F, const int* ldF, cons
 
 // ---- Gram on the tensor cores (tk_gram_tc.cu) ----
 bool tk_gram_tc_supported(int Khat);
-int tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, size_t Wpart_elems, cudaStream_t s);
+// W (FP64, Khat x Khat) = Z^T Z via per-CTA partials in Wpart (>= sm_count 128 x 128 tiles)
+void tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, size_t Wpart_elems, double* W,
+                cudaStream_t s);
 
 // ---- factor update (tk_factor.cu) ----
 void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, double* sigma_out,

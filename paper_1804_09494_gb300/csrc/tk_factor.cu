@@ -1142,6 +1142,147 @@ __global__ void __launch_bounds__(128) k_backproj_tile(const T* __restrict__ Z, 
   }
 }
 
+// FP32 back-projection U = Z Vs (Vs = V Sigma^-1) fused with the first
+// CholeskyQR Gram, with the tile stream in flight: each CTA walks 128-row tiles
+// of Z (one contiguous span each), loaded by bulk async copies into two
+// buffers while the other is consumed.  Thread r computes row r of the tile
+// from 16-byte reads of its row (the unpadded 4 * Khat-byte stride keeps the
+// eight lanes of each read phase on distinct banks) and broadcast reads of Vs.
+// Waits are bounded; a timeout sets TK_DEV_ERR_TIMEOUT.
+template <int KM>
+__global__ void __launch_bounds__(128) k_backproj_bulk(const float* __restrict__ Z, int R, int Khat,
+                                                       const float* __restrict__ Vs, int K, float* __restrict__ U,
+                                                       double* __restrict__ Cpart, int* err) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NP = KM * (KM + 1) / 2;
+  constexpr int KP = (KM + 3) / 4 * 4;
+  __shared__ float wsum[4][NP];
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ int s_fail;
+  float* vs = (float*)smraw;        // Khat x KP
+  float* tiles = vs + Khat * KP;    // 2 x 128 x Khat
+  const int tid = threadIdx.x;
+  const int ntile = (R + 127) / 128;
+  for (int i = tid; i < Khat * KP; i += 128) {
+    const int cc = i / KP, k = i - cc * KP;
+    vs[i] = k < K ? Vs[cc * K + k] : 0.f;
+  }
+  if (tid == 0) {
+    s_fail = 0;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(&full[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(&full[1])), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  int issued = 0;  // thread 0: tiles issued
+  auto issue = [&](int i) {
+    const int t = blockIdx.x + i * gridDim.x;
+    if (t >= ntile) return;
+    const int rows = min(128, R - t * 128);
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(&full[i & 1]);
+    const unsigned bytes = (unsigned)(rows * Khat * 4);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(tiles + (size_t)(i & 1) * 128 * Khat)),
+                 "l"(Z + (int64_t)t * 128 * Khat), "r"(bytes), "r"(bar)
+                 : "memory");
+    issued = i + 1;
+  };
+  auto wait_full = [&](int i) -> bool {
+    const unsigned bar = (unsigned)__cvta_generic_to_shared(&full[i & 1]);
+    const unsigned par = (unsigned)((i >> 1) & 1);
+    uint32_t done = 0;
+    const long long t0 = clock64();
+    while (!done) {
+      asm volatile(
+          "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
+          : "=r"(done)
+          : "r"(bar), "r"(par)
+          : "memory");
+      if (!done && clock64() - t0 > 4000000000LL) return false;
+    }
+    return true;
+  };
+  if (tid == 0) {
+    issue(0);
+    issue(1);
+  }
+  float g[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) g[q] = 0.f;
+  int i = 0;
+  for (; blockIdx.x + i * gridDim.x < ntile; ++i) {
+    const int t = blockIdx.x + i * gridDim.x;
+    if (!wait_full(i)) atomicOr(&s_fail, 1);
+    __syncthreads();
+    if (s_fail) break;
+    const int nr = min(128, R - t * 128);
+    if (tid < nr) {
+      float u[KP];
+#pragma unroll
+      for (int k = 0; k < KP; ++k) u[k] = 0.f;
+      const float4* zr = reinterpret_cast<const float4*>(tiles + (size_t)(i & 1) * 128 * Khat + (size_t)tid * Khat);
+#pragma unroll 2
+      for (int c4 = 0; c4 < Khat / 4; ++c4) {
+        const float4 z = zr[c4];
+        const float zz[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float4* v = reinterpret_cast<const float4*>(vs + (size_t)(4 * c4 + e) * KP);
+#pragma unroll
+          for (int q = 0; q < KP / 4; ++q) {
+            const float4 x = v[q];
+            u[4 * q + 0] = fmaf(zz[e], x.x, u[4 * q + 0]);
+            u[4 * q + 1] = fmaf(zz[e], x.y, u[4 * q + 1]);
+            u[4 * q + 2] = fmaf(zz[e], x.z, u[4 * q + 2]);
+            u[4 * q + 3] = fmaf(zz[e], x.w, u[4 * q + 3]);
+          }
+        }
+      }
+      float* ur = U + ((int64_t)t * 128 + tid) * K;
+#pragma unroll
+      for (int k = 0; k < KM; ++k)
+        if (k < K) ur[k] = u[k];
+      int q = 0;
+#pragma unroll
+      for (int x = 0; x < KM; ++x)
+#pragma unroll
+        for (int y = x; y < KM; ++y) {
+          g[q] = fmaf(u[x], u[y], g[q]);
+          ++q;
+        }
+    }
+    __syncthreads();  // buffer i & 1 is free
+    if (tid == 0) issue(i + 2);
+  }
+  if (s_fail && tid == 0) {
+    for (int x = i; x < issued; ++x) wait_full(x);  // copies in flight land before the CTA exits
+    atomicOr(err, TK_DEV_ERR_TIMEOUT);
+  }
+  const int lane = tid & 31, w = tid >> 5;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    float v = g[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[w][q] = v;
+  }
+  __syncthreads();
+  for (int q = tid; q < NP; q += 128) {
+    int x = 0, rem = q;
+    while (rem >= KM - x) {
+      rem -= KM - x;
+      ++x;
+    }
+    const int y = x + rem;
+    if (x < K && y < K) {
+      const double sum = (double)wsum[0][q] + (double)wsum[1][q] + (double)wsum[2][q] + (double)wsum[3][q];
+      Cpart[(int64_t)blockIdx.x * K * K + x * K + y] = sum;
+      Cpart[(int64_t)blockIdx.x * K * K + y * K + x] = sum;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ CholeskyQR2
 // Per-block partial of (U M)^T (U M): batches of 64 rows are transformed into
 // shared memory, each thread sums its (a,b) pairs over a batch in T and adds
@@ -1448,11 +1589,8 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
   bool gram_done = false;
   if constexpr (sizeof(T) == 4) {
     if (tk_gram_tc_supported(Khat) && ((uintptr_t)Z % 16 == 0)) {
-      // tensor cores: per-CTA partials of the full 128 x 128 tile, reduced in FP64
-      const int nsplit = tk_gram_tc(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->Wpart_elems, s);
-      const unsigned g2 = (unsigned)std::min<int64_t>(tk_ceil_div((int64_t)Khat * Khat * 8, 256), 8192);
-      k_gram_reduce<T><<<g2, 256, 0, s>>>((const T*)ws->Wpart, nsplit, 1, 1, 128, Khat, ws->W);
-      TK_CUDA(cudaGetLastError());
+      // tensor cores: per-CTA partials, reduced and symmetrised in FP64
+      tk_gram_tc(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->Wpart_elems, ws->W, s);
       tk_launched(c, PH_GRAM, 2);
       gram_done = true;
     }
@@ -1527,7 +1665,24 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     double* sign = ws->Rinv + 2 * TK_MAXK * TK_MAXK;
     const size_t tshm = ((size_t)Khat * 16 + (size_t)128 * (Khat + 1)) * sizeof(T);
     int nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 128), 4 * sms));
-    if (K <= (sizeof(T) == 4 ? 16 : 12) && tshm <= 200 * 1024) {
+    const size_t bshm = ((size_t)Khat * 12 + (size_t)2 * 128 * Khat) * 4;
+    bool bulk = false;
+    if constexpr (sizeof(T) == 4) {
+      bulk = K <= 12 && Khat % 4 == 0 && ((uintptr_t)Z % 16) == 0 && bshm <= 110 * 1024;
+    }
+    if (bulk) {
+      if constexpr (sizeof(T) == 4) {
+        nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 128), 2 * sms));
+        if (K <= 8) {
+          set_tile_attr(k_backproj_bulk<8>, bshm);
+          k_backproj_bulk<8><<<nblk, 128, bshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart, c->err);
+        } else {
+          set_tile_attr(k_backproj_bulk<12>, bshm);
+          k_backproj_bulk<12><<<nblk, 128, bshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart, c->err);
+        }
+        TK_CUDA(cudaGetLastError());
+      }
+    } else if (K <= (sizeof(T) == 4 ? 16 : 12) && tshm <= 200 * 1024) {
       // tiled back-projection fused with the first CholeskyQR Gram
       if (K <= 8) {
         set_tile_attr(k_backproj_tile<T, 8, true>, tshm);

@@ -2,23 +2,31 @@
 // tensor cores (tcgen05, kind::tf32) -- the FP32 context's first factor-update
 // step.  Z is R x Khat (row-major FP32, Khat <= 128, Khat % 4 == 0).
 //
+// Each value is split into hi = TF32(z) (mantissa truncated) and lo = z - hi
+// (exact in FP32).  Since hi^T hi is symmetric,
+//     W = hi^T hi + hi^T lo + lo^T hi = sym(D),  D = hi^T hi + hi^T (2 lo),
+// with sym(D) = (D + D^T) / 2: two MMAs per K-step instead of three, the
+// symmetrisation done in the final FP64 reduction (lo^T lo, below FP32
+// resolution, is dropped).
+//
 // One persistent CTA per SM takes a contiguous range of rows.  Per batch of 32
 // rows:
-//   * the raw rows (one contiguous span) arrive in shared memory through a
-//     4-deep cp.async pipeline;
+//   * the rows (one contiguous span) arrive by a bulk async copy into one of 8
+//     raw stages (mbarrier with transaction count), issued 8 batches ahead;
 //   * 256 threads transpose them into the K-major, 128-byte-swizzled operand
-//     layout (M = Z's column index padded to 128, K = the batch's 32 rows),
-//     splitting each value into hi = TF32(z) (mantissa truncated) and
-//     lo = z - hi (exact in FP32);
-//   * one thread issues 4 K-steps x 3 MMAs, D += hi hi^T + hi lo^T + lo hi^T,
-//     into a 128 x 128 FP32 accumulator in tensor memory, and commits them to
-//     the stage's mbarrier (which also frees the operand stage for reuse).
-// Every 8 batches (256 rows) the accumulator is read back (tcgen05.ld) and
-// added with Kahan compensation into per-CTA sums in shared memory, so each
-// FP32 sum inside the tensor core covers at most 256 rows.  The CTA finally
-// writes its partial W; partials are reduced in FP64 in a fixed order.
-// Every mbarrier wait is bounded; a timeout sets TK_DEV_ERR_TIMEOUT and the
-// kernel releases its tensor memory and returns.
+//     layout (M = Z's column index padded to 128, K = the batch's rows) as hi
+//     and 2 lo;
+//   * one thread issues 4 K-steps x 2 MMAs into one of two 128-column FP32
+//     accumulators in tensor memory and commits them to the operand stage's
+//     mbarrier.
+// The accumulators alternate every 8 batches (256 rows): while the tensor core
+// fills one, the threads read the other back (tcgen05.ld) and add it with
+// Kahan compensation into per-thread register sums -- each thread's fragment
+// is exactly the 64 entries it owns -- so every FP32 sum inside the tensor
+// core covers at most 256 rows.  Partials are reduced in FP64 in a fixed
+// order.  Every mbarrier wait is bounded; a timeout sets TK_DEV_ERR_TIMEOUT and
+// the CTA waits (bounded) for its copies and MMAs in flight, releases its
+// tensor memory and returns.
 #include <algorithm>
 
 #include "tk_common.cuh"
@@ -27,9 +35,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kBatch = 32;        // rows of Z per MMA batch (one 128-byte swizzle atom of K)
-constexpr int kDrainEvery = 8;    // batches per TMEM drain
-constexpr int kRaw = 4;           // raw-row pipeline depth
+constexpr int kDrainEvery = 8;    // batches per accumulator group
+constexpr int kRaw = 8;           // raw-row stages (bulk copies in flight)
 constexpr int kOpBytes = 128 * kBatch * 4;  // one 128 x 32 FP32 operand tile (16 KB)
+constexpr int kTmemCols = 256;    // two 128-column accumulators
 constexpr long long kWaitCycles = 4000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -49,17 +58,24 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
   return d;
 }
 
-// kind::tf32 instruction descriptor: D FP32, A and B TF32 K-major, M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// kind::tf32 instruction descriptor: D FP32, A and B TF32 K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
+}
+
+__device__ __forceinline__ bool mbar_wait(const uint64_t* bar, uint32_t parity) {
+  const uint32_t addr = smem_u32(bar);
   uint32_t done = 0;
   const long long t0 = clock64();
   while (!done) {
@@ -73,15 +89,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
   return true;
 }
 
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+// bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) into
+// shared memory, completing on `bar`
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 struct GramTcArgs {
   const float* Z;
   int R, Khat;
   int rows_per_cta;
-  float* Wpart;  // gridDim.x x 128 x 128
+  float* Wpart;  // gridDim.x x 128 x 128: D of each CTA
   int* err;
 };
 
@@ -90,167 +112,214 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const GramTcArgs a) {
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   const int Khat = a.Khat;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // layout: operands [2 stages][hi, lo] | raw [kRaw][kBatch][Khat] | acc, cmp [Khat][Khat+1] | barriers
+  // layout: operands [2 stages][hi, 2 lo] | raw [kRaw][kBatch][Khat] | barriers | TMEM slot
   unsigned char* ops = sm;
   float* raw = (float*)(sm + 4 * kOpBytes);
   const int rawStage = kBatch * Khat;  // floats
-  float* acc = raw + kRaw * rawStage;
-  const int ldA = Khat + 1;
-  float* cmp = acc + Khat * ldA;
-  uint64_t* mbar = (uint64_t*)(((uintptr_t)(cmp + Khat * ldA) + 15) & ~(uintptr_t)15);
-  uint32_t* tslot = (uint32_t*)(mbar + 2);
+  uint64_t* raw_full = (uint64_t*)(raw + kRaw * rawStage);
+  uint64_t* op_free = raw_full + kRaw;
+  uint64_t* acc_done = op_free + 2;
+  uint32_t* tslot = (uint32_t*)(acc_done + 2);
   __shared__ int s_fail;
 
   const int64_t r0 = (int64_t)blockIdx.x * a.rows_per_cta;
   const int64_t r1 = min((int64_t)a.R, r0 + a.rows_per_cta);
   const int nrows = (int)max((int64_t)0, r1 - r0);
   const int nb = (nrows + kBatch - 1) / kBatch;
+  const int ncols = (Khat + 15) & ~15;  // MMA N
+  const uint32_t idesc = idesc_tf32(ncols);
 
-  for (int i = tid; i < Khat * ldA; i += kThreads) {
-    acc[i] = 0.f;
-    cmp[i] = 0.f;
-  }
-  // zero the operand tiles once: padding columns (m >= Khat) stay zero
+  // zero the operand tiles once: padding rows m >= Khat stay zero
   for (int i = tid; i < 4 * kOpBytes / 16; i += kThreads) reinterpret_cast<float4*>(ops)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   if (tid == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+    for (int i = 0; i < kRaw + 4; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&raw_full[i])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(128));
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = *tslot;
 
+  // thread 0 only
+  int issued = 0;   // raw batches issued
+  int mma_last = -1;  // last batch whose MMAs were issued
   auto issue_raw = [&](int b) {
-    if (b < nb) {
-      const int rows = min(kBatch, nrows - b * kBatch);
-      const float* src = a.Z + (r0 + (int64_t)b * kBatch) * Khat;
-      float* dst = raw + (b % kRaw) * rawStage;
-      const int n16 = rows * Khat / 4;
-      for (int q = tid; q < n16; q += kThreads) cp_async16(dst + 4 * q, src + 4 * q);
-    }
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    const int rows = min(kBatch, nrows - b * kBatch);
+    bulk_load(raw + (b % kRaw) * rawStage, a.Z + (r0 + (int64_t)b * kBatch) * Khat, (uint32_t)(rows * Khat * 4),
+              &raw_full[b % kRaw]);
+    issued = b + 1;
   };
-  for (int b = 0; b < kRaw - 1; ++b) issue_raw(b);
+  if (tid == 0)
+    for (int b = 0; b < min(kRaw, nb); ++b) issue_raw(b);
 
-  bool ok = true;
-  for (int b = 0; b < nb && ok; ++b) {
-    issue_raw(b + kRaw - 1);
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(kRaw - 1) : "memory");
-    __syncthreads();
-    const int st = b & 1;
-    if (b >= 2 && !mbar_wait(smem_u32(&mbar[st]), ((b - 2) >> 1) & 1)) ok = false;
-    if (!ok) {
+  // Kahan sums of the 64 accumulator entries this thread reads back:
+  // D row 32 * (warp % 4) + lane, columns 64 * (warp / 4) + [0, 64)
+  float sacc[64], scmp[64];
+#pragma unroll
+  for (int j = 0; j < 64; ++j) {
+    sacc[j] = 0.f;
+    scmp[j] = 0.f;
+  }
+  auto drain = [&](int G) -> bool {
+    if (!mbar_wait(&acc_done[G & 1], (uint32_t)((G >> 1) & 1))) return false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((G & 1) * 128 + 64 * (warp >> 2));
+#pragma unroll
+    for (int cc = 0; cc < 64; cc += 16) {
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(base + (uint32_t)cc));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float y = __uint_as_float(v[j]) - scmp[cc + j];
+        const float t = sacc[cc + j] + y;
+        scmp[cc + j] = (t - sacc[cc + j]) - y;
+        sacc[cc + j] = t;
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    return true;
+  };
+
+  // this thread's (column m, 4-row chunk) pairs of the transposition, the same
+  // for every batch: at most kPairs per thread (Khat * kBatch / 4 <= 1024)
+  constexpr int kPairs = 128 * (kBatch / 4) / kThreads;
+  int pm[kPairs], pc[kPairs];
+  uint32_t poff[kPairs];
+#pragma unroll
+  for (int i = 0; i < kPairs; ++i) {
+    const int pidx = tid + i * kThreads;
+    pm[i] = pidx < Khat * (kBatch / 4) ? pidx % Khat : -1;
+    pc[i] = pidx / Khat;
+    poff[i] = pm[i] >= 0 ? sw128_off(pm[i], 4 * pc[i]) : 0u;
+  }
+
+  int b = 0;
+  for (; b < nb; ++b) {
+    const int slot = b % kRaw, st = b & 1;
+    bool okb = mbar_wait(&raw_full[slot], (uint32_t)((b / kRaw) & 1));
+    // operand stage st is free once the MMAs of batch b - 2 are done
+    if (okb && b >= 2) okb = mbar_wait(&op_free[st], (uint32_t)(((b - 2) >> 1) & 1));
+    if (!okb) {
       atomicOr(&s_fail, 1);
     } else {
-      // transpose + split: thread handles (column m, 4-row chunk c)
       const int rows = min(kBatch, nrows - b * kBatch);
-      const float* rw = raw + (b % kRaw) * rawStage;
+      const float* rw = raw + slot * rawStage;
       unsigned char* hi = ops + st * 2 * kOpBytes;
       unsigned char* lo = hi + kOpBytes;
-      for (int pidx = tid; pidx < Khat * (kBatch / 4); pidx += kThreads) {
-        const int m = pidx % Khat, cch = pidx / Khat;
+      float zv[kPairs][4];
+#pragma unroll
+      for (int i = 0; i < kPairs; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = 4 * pc[i] + q;
+          zv[i][q] = (pm[i] >= 0 && r < rows) ? rw[r * Khat + pm[i]] : 0.f;
+        }
+#pragma unroll
+      for (int i = 0; i < kPairs; ++i) {
+        if (pm[i] < 0) continue;
         float h4[4], l4[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int r = 4 * cch + q;
-          const float z = r < rows ? rw[r * Khat + m] : 0.f;
-          const float h = __uint_as_float(__float_as_uint(z) & 0xFFFFE000u);
+          const float h = __uint_as_float(__float_as_uint(zv[i][q]) & 0xFFFFE000u);
           h4[q] = h;
-          l4[q] = z - h;
+          l4[q] = 2.f * (zv[i][q] - h);
         }
-        const uint32_t off = sw128_off(m, 4 * cch);
-        *reinterpret_cast<float4*>(hi + off) = make_float4(h4[0], h4[1], h4[2], h4[3]);
-        *reinterpret_cast<float4*>(lo + off) = make_float4(l4[0], l4[1], l4[2], l4[3]);
+        *reinterpret_cast<float4*>(hi + poff[i]) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+        *reinterpret_cast<float4*>(lo + poff[i]) = make_float4(l4[0], l4[1], l4[2], l4[3]);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    if (s_fail) {
-      ok = false;
-      break;
-    }
+    if (s_fail) break;
     if (tid == 0) {
+      // raw stage `slot` is free: every thread has passed its reads
+      if (b + kRaw < nb) issue_raw(b + kRaw);
       asm volatile("tcgen05.fence::after_thread_sync;");
+      const int G = b / kDrainEvery;
+      const uint32_t dacc = tmem + (uint32_t)((G & 1) * 128);
       const uint64_t dh = sdesc_sw128(smem_u32(ops + st * 2 * kOpBytes));
       const uint64_t dl = sdesc_sw128(smem_u32(ops + st * 2 * kOpBytes + kOpBytes));
       const bool first = (b % kDrainEvery) == 0;
 #pragma unroll
       for (int s = 0; s < kBatch / 8; ++s) {
         const uint64_t k = (uint64_t)(2 * s);  // +32 bytes per K-step of 8
-        mma_tf32(tmem, dh + k, dh + k, (first && s == 0) ? 0u : 1u);
-        mma_tf32(tmem, dh + k, dl + k, 1u);
-        mma_tf32(tmem, dl + k, dh + k, 1u);
+        mma_tf32(dacc, dh + k, dh + k, idesc, (first && s == 0) ? 0u : 1u);
+        mma_tf32(dacc, dh + k, dl + k, idesc, 1u);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar[st])));
+      mma_commit(&op_free[st]);
+      if ((b % kDrainEvery) == kDrainEvery - 1 || b == nb - 1) mma_commit(&acc_done[G & 1]);
+      mma_last = b;
     }
-    if ((b % kDrainEvery) == kDrainEvery - 1 || b == nb - 1) {
-      if (!mbar_wait(smem_u32(&mbar[st]), (b >> 1) & 1)) atomicOr(&s_fail, 1);
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      __syncthreads();
-      if (!s_fail) {
-        // warp w reads TMEM lanes 32*(w%4).. and columns 64*(w/4)..; lane = row of D
-        const int row = 32 * (warp & 3) + lane;
-        const int c0 = 64 * (warp >> 2);
-#pragma unroll
-        for (int cc = 0; cc < 64; cc += 16) {
-          uint32_t v[16];
-          const uint32_t taddr = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)(c0 + cc);
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-              "[%16];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                "=r"(v[15])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (row < Khat) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const int col = c0 + cc + j;
-              if (col < Khat) {
-                float* sp = acc + row * ldA + col;
-                float* cp = cmp + row * ldA + col;
-                const float y = __uint_as_float(v[j]) - *cp;
-                const float t = *sp + y;
-                *cp = (t - *sp) - y;
-                *sp = t;
-              }
-            }
-          }
-        }
-      }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncthreads();
-      if (s_fail) {
-        ok = false;
-        break;
-      }
-    }
+    // read back the previous group while this group's first MMAs run
+    if ((b % kDrainEvery) == 0 && b > 0)
+      if (!drain(b / kDrainEvery - 1)) atomicOr(&s_fail, 1);
   }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  if (!s_fail && nb > 0)
+    if (!drain((nb - 1) / kDrainEvery)) atomicOr(&s_fail, 1);
   __syncthreads();
-  if (!ok || s_fail) {
-    if (tid == 0) atomicOr(a.err, TK_DEV_ERR_TIMEOUT);
+  const bool failed = s_fail != 0;
+  if (tid == 0 && failed) {
+    // let the copies and MMAs in flight finish (bounded) before the memory goes away
+    for (int x = max(0, b); x < issued; ++x) mbar_wait(&raw_full[x % kRaw], (uint32_t)((x / kRaw) & 1));
+    if (mma_last >= 0) mbar_wait(&op_free[mma_last & 1], (uint32_t)((mma_last >> 1) & 1));
+    atomicOr(a.err, TK_DEV_ERR_TIMEOUT);
   }
   float* out = a.Wpart + (int64_t)blockIdx.x * 128 * 128;
-  for (int i = tid; i < 128 * 128; i += kThreads) {
-    const int r = i >> 7, cc = i & 127;
-    out[i] = (r < Khat && cc < Khat) ? acc[r * ldA + cc] : 0.f;
+  {
+    const int row = 32 * (warp & 3) + lane, c0 = 64 * (warp >> 2);
+#pragma unroll
+    for (int j = 0; j < 64; j += 4) {
+      float4 v = make_float4(sacc[j], sacc[j + 1], sacc[j + 2], sacc[j + 3]);
+      if (failed) v = make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(out + row * 128 + c0 + j) = v;
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// W[i][j] = (S[i][j] + S[j][i]) / 2 with S = sum of the CTA partials in split
+// order (FP64); 8 lanes per entry, each over every 8th split, combined by a
+// fixed shuffle tree.
+__global__ void k_gram_tc_reduce(const float* __restrict__ Wpart, int nsplit, int Khat, double* __restrict__ W) {
+  const int64_t total = (int64_t)Khat * Khat;
+  const int part = threadIdx.x & 7;
+  const int64_t per_pass = ((int64_t)gridDim.x * blockDim.x) >> 3;
+  for (int64_t base = 0; base < total; base += per_pass) {  // uniform trip count for every lane
+    const int64_t idx0 = base + (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 3);
+    const bool live = idx0 < total;
+    const int64_t idx = live ? idx0 : 0;
+    const int i = (int)(idx / Khat), j = (int)(idx - (int64_t)i * Khat);
+    double s = 0.0, t = 0.0;
+    if (live)
+      for (int sp = part; sp < nsplit; sp += 8) {
+        s += (double)Wpart[(int64_t)sp * 128 * 128 + i * 128 + j];
+        t += (double)Wpart[(int64_t)sp * 128 * 128 + j * 128 + i];
+      }
+    s += t;
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (part == 0 && live) W[idx] = 0.5 * s;
+  }
 }
 
 size_t smem_bytes(int Khat) {
-  return 1024 + (size_t)4 * kOpBytes + (size_t)kRaw * kBatch * Khat * 4 + (size_t)2 * Khat * (Khat + 1) * 4 + 64;
+  return 1024 + (size_t)4 * kOpBytes + (size_t)kRaw * kBatch * Khat * 4 + (size_t)8 * (kRaw + 4) + 16;
 }
 
 }  // namespace
@@ -259,8 +328,9 @@ bool tk_gram_tc_supported(int Khat) {
   return Khat >= 8 && Khat <= 128 && Khat % 4 == 0 && smem_bytes(Khat) <= 225 * 1024;
 }
 
-// Writes gridDim partials of W (128 x 128 FP32 tiles) into Wpart; returns the number of partials.
-int tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, size_t Wpart_elems, cudaStream_t s) {
+// W (Khat x Khat FP64) = Z^T Z; Wpart holds the per-CTA partials (128 x 128 FP32 each).
+void tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, size_t Wpart_elems, double* W,
+                cudaStream_t s) {
   int nblk = std::max(1, std::min(c->sm_count, (int)tk_ceil_div(R, 1024)));
   while ((size_t)nblk * 128 * 128 > Wpart_elems && nblk > 1) --nblk;
   GramTcArgs a{};
@@ -279,5 +349,7 @@ int tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, siz
   }
   k_gram_tc<<<nblk, kThreads, shm, s>>>(a);
   TK_CUDA(cudaGetLastError());
-  return nblk;
+  const unsigned g2 = (unsigned)std::min<int64_t>(tk_ceil_div((int64_t)Khat * Khat * 8, 256), 8192);
+  k_gram_tc_reduce<<<g2, 256, 0, s>>>(Wpart, nblk, Khat, W);
+  TK_CUDA(cudaGetLastError());
 }
