@@ -13,6 +13,7 @@ oracle instead, on a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -120,6 +121,8 @@ def ttm_bytes_flops(w, R, n):
 
 
 def core_mode(w, R):
+    """The mode whose TTM-chain forms the core (the library's rule: smallest
+    Khat, then the fewest non-empty slices)."""
     K = w["K"]
     N = len(K)
     kh = [int(np.prod([K[m] for m in range(N) if m != n])) for n in range(N)]
@@ -152,6 +155,32 @@ def oracle_sample_seconds(w, sample):
         if r.returncode != 0:
             raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
         return float(r.stdout.strip().splitlines()[-1])
+
+
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_ttmc_fwd_dram_zipf1.1-2Mx1Mx50K-nnz100M.md")
+# the counters hold for these sources (the kernel and the choice of the core's chain)
+TTMC_SOURCES = [os.path.join(ROOT, "paper_1804_09494_gb300", "csrc", f) for f in ("tk_ttmc.cu", "tk_core.cu")]
+
+
+def ttm_traffic_per_launch(args):
+    """DRAM bytes (read + write) per TTM-chain launch from the committed ncu
+    summary of the full-size workload; None for another workload or when the
+    kernel source has changed since the counters were taken."""
+    if args.workload != WORKLOAD or args.nnz is not None or not os.path.exists(TRAFFIC_PROFILE):
+        return None
+    val, sha = None, {}
+    with open(TRAFFIC_PROFILE) as f:
+        for line in f:
+            if line.startswith("traffic_bytes_per_launch:"):
+                val = int(line.split(":")[1])
+            elif " sha256:" in line:
+                name, h = line.split(" sha256:")
+                sha[name.strip()] = h.strip()
+    for path in TTMC_SOURCES:
+        with open(path, "rb") as f:
+            if sha.get(os.path.basename(path)) != hashlib.sha256(f.read()).hexdigest():
+                return None
+    return val
 
 
 def load_workload(args):
@@ -229,10 +258,12 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
+    torch.cuda.nvtx.range_push("timed")  # profilers can restrict a capture to this range
     e0.record(stream)
     for s in range(args.steps):
         _, fit = tk.hooi_iter(F, G, want_fit=(s == args.steps - 1))
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     ck = clocks.stop()
     t_loc = e0.elapsed_time(e1) / 1e3
@@ -260,6 +291,7 @@ def run_ours(args):
     launches_per_iter = ttm_launches / args.steps
     bytes_per_launch = per_iter_bytes / launches_per_iter
     achieved_gbs = bytes_per_launch / ttm_s_per_launch / 1e9
+    traffic = ttm_traffic_per_launch(args)
     fp32_peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     achieved_tflops = per_iter_flops / launches_per_iter / ttm_s_per_launch / 1e12
 
@@ -270,15 +302,21 @@ def run_ours(args):
     h2d = sum(f.numel() * 4 for f in Fh)
     d2h = h2d + Gh.numel() * 4 + 8
     e2e_steps = max(1, min(args.steps, 20))
-    barrier()
-    e0.record(stream)
-    for _ in range(e2e_steps):
+
+    def e2e_step():
         for fd, fh in zip(F, Fh):
             fd.copy_(fh, non_blocking=True)
         _, fit_e2e = tk.hooi_iter(F, G, want_fit=True)  # the fit is read back to the host
         for fo, fd in zip(Fo, F):
             fo.copy_(fd, non_blocking=True)
         Gh.copy_(G, non_blocking=True)
+
+    for _ in range(max(1, min(args.warmup, 3))):  # first use of the pinned buffers is not timed
+        e2e_step()
+    barrier()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
     e1.record(stream)
     barrier()
     e2e_s = e0.elapsed_time(e1) / 1e3 / e2e_steps
@@ -329,7 +367,7 @@ def run_ours(args):
                         l2="inputs larger than L2 (permuted copies ~6 GB per context)",
                         parallelism="replicas" if world > 1 else "single GPU"),
             roofline=dict(bound="hbm", achieved=round(achieved_gbs, 1), peak=pk["hbm_gbs"], unit="GB/s",
-                          frac=round(achieved_gbs / pk["hbm_gbs"], 4), traffic=None,
+                          frac=round(achieved_gbs / pk["hbm_gbs"], 4), traffic=traffic,
                           kernel="k_ttmc_fwd", peak_source=pk["source"] + " (hbm_gbs)",
                           bytes_per_launch=int(bytes_per_launch), ms_per_launch=round(ttm_s_per_launch * 1e3, 4),
                           alu_tflops=round(achieved_tflops, 2), alu_frac_fp32=round(achieved_tflops / fp32_peak_tflops, 4)),
