@@ -61,7 +61,14 @@ typedef struct {
   int32_t gauss_seidel;  /* 0 = Fig. 1 as printed (every mode from the input factors),     *
                           * 1 = textbook HOOI (each mode sees the factors refined so far) */
   int32_t timing;        /* 1 = record CUDA events around every phase (tucker_timings)    */
-  int32_t reserved[8];   /* must be zero                                                  */
+  int32_t wait_cap;      /* polls allowed per device wait (the mbarrier waits of the       *
+                          * tensor-core Gram and of the bulk-copy back-projection) before *
+                          * the wait is abandoned with TUCKER_ERR_TIMEOUT; 0 = no poll    *
+                          * limit (each wait is still bounded by ~4e9 clock cycles);      *
+                          * -1 = abandon every such wait at once (fault injection: runs   *
+                          * the timeout path -- copies and MMAs in flight are still       *
+                          * awaited -- with no stuck wait)                                */
+  int32_t reserved[7];   /* must be zero                                                  */
 } tucker_opts;
 
 /* Fills *opts with the defaults (FP32, automatic P, Jacobi reading, no timing). */

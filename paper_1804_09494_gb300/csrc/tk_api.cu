@@ -37,10 +37,11 @@ void check_device_error(tucker_ctx* c, cudaStream_t s) {
   if (h) {
     TK_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), s));
     TK_CUDA(cudaStreamSynchronize(s));
+    // a timed-out wait leaves partial results behind, so it is reported first
+    if (h & TK_DEV_ERR_TIMEOUT) tk_throw(TUCKER_ERR_TIMEOUT, "a bounded device wait ran out");
     if (h & TK_DEV_ERR_NUMERIC) tk_throw(TUCKER_ERR_NUMERIC, "numeric breakdown (rank-deficient factor update)");
     if (h & TK_DEV_ERR_NONFINITE) tk_throw(TUCKER_ERR_ARG, "non-finite tensor value");
     if (h & TK_DEV_ERR_INDEX) tk_throw(TUCKER_ERR_INDEX, "coordinate out of range");
-    if (h & TK_DEV_ERR_TIMEOUT) tk_throw(TUCKER_ERR_TIMEOUT, "a bounded device wait ran out");
     tk_throw(TUCKER_ERR_STATE, "device error word " + std::to_string(h));
   }
 }
@@ -196,7 +197,8 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     if (nnz < 1 || nnz >= ((int64_t)1 << 31) - 1) tk_throw(TUCKER_ERR_ARG, "nnz must be in [1, 2^31 - 1)");
     if (o.prec != TUCKER_FP32 && o.prec != TUCKER_FP64) tk_throw(TUCKER_ERR_ARG, "unknown precision");
     if (o.P_bins < 0) tk_throw(TUCKER_ERR_ARG, "P_bins must be >= 0");
-    for (int i = 0; i < 8; ++i)
+    if (o.wait_cap < -1) tk_throw(TUCKER_ERR_ARG, "wait_cap must be >= -1");
+    for (int i = 0; i < 7; ++i)
       if (o.reserved[i]) tk_throw(TUCKER_ERR_ARG, "reserved option fields must be zero");
     for (int m = 0; m < N; ++m) {
       if (L[m] < 1 || L[m] >= ((int64_t)1 << 31) - 1) tk_throw(TUCKER_ERR_ARG, "mode length out of range");
@@ -211,6 +213,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     c->esz = o.prec == TUCKER_FP32 ? 4 : 8;
     c->gauss_seidel = o.gauss_seidel != 0;
     c->timing = o.timing != 0;
+    c->wait_cap = o.wait_cap;
     c->sm_count = tk_sm_count();
     for (int m = 0; m < N; ++m) {
       c->L[m] = L[m];

@@ -120,6 +120,7 @@ struct tucker_ctx {
   double* Zchunk = nullptr; // max_n nchunks * Khat_n
   tk_fuws fu[TK_MAXN];      // factor-update workspace, one per mode (modes overlap on side streams)
   void* Zm[TK_MAXN] = {};   // per-mode penultimate matrices (R_n x Khat_n)
+  int wait_cap = 0;         // polls per device wait (0: time bound only, -1: abandon at once)
   void* Zcore = nullptr;    // the core's penultimate matrix (mode tk_core_mode), apart from
                             // Zm so that it can be formed while that mode's update reads Zm
   cudaStream_t aux[TK_MAXN] = {};

@@ -1152,7 +1152,7 @@ __global__ void __launch_bounds__(128) k_backproj_tile(const T* __restrict__ Z, 
 template <int KM>
 __global__ void __launch_bounds__(128) k_backproj_bulk(const float* __restrict__ Z, int R, int Khat,
                                                        const float* __restrict__ Vs, int K, float* __restrict__ U,
-                                                       double* __restrict__ Cpart, int* err) {
+                                                       double* __restrict__ Cpart, int* err, int cap) {
   extern __shared__ __align__(16) unsigned char smraw[];
   constexpr int NP = KM * (KM + 1) / 2;
   constexpr int KP = (KM + 3) / 4 * 4;
@@ -1188,18 +1188,21 @@ __global__ void __launch_bounds__(128) k_backproj_bulk(const float* __restrict__
                  : "memory");
     issued = i + 1;
   };
-  auto wait_full = [&](int i) -> bool {
+  // bounded by ~4e9 cycles and, if pcap > 0, by pcap polls; pcap < 0 abandons
+  // the wait at once (fault injection)
+  auto wait_full = [&](int i, int pcap) -> bool {
+    if (pcap < 0) return false;
     const unsigned bar = (unsigned)__cvta_generic_to_shared(&full[i & 1]);
     const unsigned par = (unsigned)((i >> 1) & 1);
     uint32_t done = 0;
     const long long t0 = clock64();
-    while (!done) {
+    for (int polls = 1; !done; ++polls) {
       asm volatile(
           "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
           : "=r"(done)
           : "r"(bar), "r"(par)
           : "memory");
-      if (!done && clock64() - t0 > 4000000000LL) return false;
+      if (!done && (clock64() - t0 > 4000000000LL || (pcap > 0 && polls >= pcap))) return false;
     }
     return true;
   };
@@ -1213,7 +1216,7 @@ __global__ void __launch_bounds__(128) k_backproj_bulk(const float* __restrict__
   int i = 0;
   for (; blockIdx.x + i * gridDim.x < ntile; ++i) {
     const int t = blockIdx.x + i * gridDim.x;
-    if (!wait_full(i)) atomicOr(&s_fail, 1);
+    if (!wait_full(i, cap)) atomicOr(&s_fail, 1);
     __syncthreads();
     if (s_fail) break;
     const int nr = min(128, R - t * 128);
@@ -1256,7 +1259,7 @@ __global__ void __launch_bounds__(128) k_backproj_bulk(const float* __restrict__
     if (tid == 0) issue(i + 2);
   }
   if (s_fail && tid == 0) {
-    for (int x = i; x < issued; ++x) wait_full(x);  // copies in flight land before the CTA exits
+    for (int x = i; x < issued; ++x) wait_full(x, 0);  // copies in flight land before the CTA exits
     atomicOr(err, TK_DEV_ERR_TIMEOUT);
   }
   const int lane = tid & 31, w = tid >> 5;
@@ -1675,10 +1678,10 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
         nblk = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 128), 2 * sms));
         if (K <= 8) {
           set_tile_attr(k_backproj_bulk<8>, bshm);
-          k_backproj_bulk<8><<<nblk, 128, bshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart, c->err);
+          k_backproj_bulk<8><<<nblk, 128, bshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart, c->err, c->wait_cap);
         } else {
           set_tile_attr(k_backproj_bulk<12>, bshm);
-          k_backproj_bulk<12><<<nblk, 128, bshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart, c->err);
+          k_backproj_bulk<12><<<nblk, 128, bshm, s>>>(Z, R, Khat, Vs, K, U, ws->Cpart, c->err, c->wait_cap);
         }
         TK_CUDA(cudaGetLastError());
       }

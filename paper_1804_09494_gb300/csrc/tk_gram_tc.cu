@@ -74,19 +74,39 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)));
 }
 
+__device__ __forceinline__ uint32_t mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return done;
+}
+
+// One thread: wait for the phase with the given parity, bounded by kWaitCycles.
 __device__ __forceinline__ bool mbar_wait(const uint64_t* bar, uint32_t parity) {
   const uint32_t addr = smem_u32(bar);
-  uint32_t done = 0;
   const long long t0 = clock64();
-  while (!done) {
-    asm volatile(
-        "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}\n"
-        : "=r"(done)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    if (!done && clock64() - t0 > kWaitCycles) return false;
-  }
+  while (!mbar_try(addr, parity))
+    if (clock64() - t0 > kWaitCycles) return false;
   return true;
+}
+
+// Whole warp (converged): the same wait with an outcome common to all lanes,
+// so that the warp-collective tcgen05 instructions after it are executed by
+// every lane or by none.  Bounded by kWaitCycles and, if cap > 0, by cap polls;
+// cap < 0 abandons the wait at once (fault injection).
+__device__ __forceinline__ bool mbar_wait_warp(const uint64_t* bar, uint32_t parity, int cap) {
+  if (cap < 0) return false;
+  const uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  for (int polls = 1;; ++polls) {
+    const uint32_t done = mbar_try(addr, parity);
+    if (__all_sync(0xffffffffu, done)) return true;
+    const bool out = clock64() - t0 > kWaitCycles || (cap > 0 && polls >= cap);
+    if (__any_sync(0xffffffffu, out)) return false;
+  }
 }
 
 // bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) into
@@ -105,6 +125,7 @@ struct GramTcArgs {
   int rows_per_cta;
   float* Wpart;  // gridDim.x x 128 x 128: D of each CTA
   int* err;
+  int cap;       // polls per wait (0: time bound only)
 };
 
 __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const GramTcArgs a) {
@@ -169,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const GramTcArgs a) {
     scmp[j] = 0.f;
   }
   auto drain = [&](int G) -> bool {
-    if (!mbar_wait(&acc_done[G & 1], (uint32_t)((G >> 1) & 1))) return false;
+    if (!mbar_wait_warp(&acc_done[G & 1], (uint32_t)((G >> 1) & 1), a.cap)) return false;
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t base = tmem + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)((G & 1) * 128 + 64 * (warp >> 2));
 #pragma unroll
@@ -209,9 +230,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const GramTcArgs a) {
   int b = 0;
   for (; b < nb; ++b) {
     const int slot = b % kRaw, st = b & 1;
-    bool okb = mbar_wait(&raw_full[slot], (uint32_t)((b / kRaw) & 1));
+    bool okb = mbar_wait_warp(&raw_full[slot], (uint32_t)((b / kRaw) & 1), a.cap);
     // operand stage st is free once the MMAs of batch b - 2 are done
-    if (okb && b >= 2) okb = mbar_wait(&op_free[st], (uint32_t)(((b - 2) >> 1) & 1));
+    if (okb && b >= 2) okb = mbar_wait_warp(&op_free[st], (uint32_t)(((b - 2) >> 1) & 1), a.cap);
     if (!okb) {
       atomicOr(&s_fail, 1);
     } else {
@@ -341,6 +362,7 @@ void tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, si
   nblk = (int)std::max<int64_t>(1, tk_ceil_div(R, a.rows_per_cta));
   a.Wpart = Wpart;
   a.err = c->err;
+  a.cap = c->wait_cap;
   const size_t shm = smem_bytes(Khat);
   static bool attr = false;
   if (!attr) {

@@ -32,7 +32,7 @@ _PD = ctypes.POINTER(ctypes.c_double)
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", _I32), ("P_bins", _I32), ("gauss_seidel", _I32), ("timing", _I32),
-                ("reserved", _I32 * 8)]
+                ("wait_cap", _I32), ("reserved", _I32 * 7)]
 
 
 SIGNATURES = {
@@ -111,7 +111,8 @@ class Tucker:
     L, K : mode lengths and core lengths
     """
 
-    def __init__(self, idx, vals, L, K, prec="fp32", P_bins=0, gauss_seidel=False, timing=False):
+    def __init__(self, idx, vals, L, K, prec="fp32", P_bins=0, gauss_seidel=False, timing=False,
+                 wait_cap=0):
         self.lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("libtucker needs a CUDA device")
@@ -131,6 +132,7 @@ class Tucker:
         opts.P_bins = int(P_bins)
         opts.gauss_seidel = int(bool(gauss_seidel))
         opts.timing = int(bool(timing))
+        opts.wait_cap = int(wait_cap)
         Ls = (ctypes.c_int64 * self.N)(*self.L)
         Ks = (ctypes.c_int32 * self.N)(*self.K)
         rows = [idx[m] for m in range(self.N)]

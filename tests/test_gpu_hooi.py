@@ -166,3 +166,27 @@ def test_mixed_and_fp64_forms_reach_the_same_fit():
     _, _, f32 = _run_hooi(c, K, F0, 3, "fp32")
     _, _, f64 = _run_hooi(c, K, F0, 3, "fp64")
     assert abs(f32[-1] - f64[-1]) <= 1e-6
+
+
+def test_forced_wait_cap_reports_timeout_and_the_gpu_stays_usable():
+    """wait_cap = -1 makes the tensor-core Gram's and the bulk-copy
+    back-projection's mbarrier waits give up at once (the copies and MMAs in
+    flight still land and are awaited before the kernels exit): the invocation
+    reports TUCKER_ERR_TIMEOUT, the error word is cleared, and a context
+    without the cap then runs the same invocation normally."""
+    from paper_1804_09494_gb300.tucker import TuckerError
+    c = case((3000, 2000, 500), 200_000, (1.1, 1.1, 1.1), "lognormal", seed=5)
+    K = (10, 10, 10)
+    Fd, Fo = factors(c["L"], K, 3, "fp32")
+    tk = make(c, K, "fp32", wait_cap=-1)
+    for _ in range(2):  # reported again on the next invocation: the context stays consistent
+        with pytest.raises(TuckerError) as e:
+            tk.hooi_iter([f.clone() for f in Fd], want_fit=True)
+        assert e.value.status == "ERR_TIMEOUT", str(e.value)
+    tk.close()
+    tk = make(c, K, "fp32")
+    _, fit = tk.hooi_iter([f.clone() for f in Fd], want_fit=True)
+    Fn = O.hooi_invocation(c["L"], c["idx"], c["vals"].astype(np.float64), Fo)
+    Go = O.core(c["L"], c["idx"], c["vals"].astype(np.float64), Fn)
+    assert abs(fit - O.fit(c["vals"].astype(np.float64), Go)) <= FIT["fp32"]
+    tk.close()
