@@ -14,8 +14,11 @@
 //
 // The kernel is bound by the latency of the two row gathers per element: the
 // F_a row is read through the LSU path and the F_b block through the texture
-// path (two L1 pipelines), and the element stream and the Z rows carry an L2
-// evict-first policy so that the reused factor rows stay in L2.
+// path (two L1 pipelines), the exact FP32 tiles of 3-mode tensors take two
+// elements per step with all four rows requested before either is used (more
+// loads in flight per SM at 8 warps than one element at 12), and the element
+// stream and the Z rows carry an L2 evict-first policy so that the reused
+// factor rows stay in L2.
 #include <algorithm>
 
 #include "tk_common.cuh"
@@ -123,6 +126,21 @@ __device__ __forceinline__ void tex_row(cudaTextureObject_t t, int64_t first, in
       for (int u = 0; u < W; ++u) out[v * W + u] = T(0);
     }
   }
+}
+
+// Loads issued in program order (volatile), so that the rows of two elements
+// are all requested before either is used.
+__device__ __forceinline__ float4 ldg_v4_ordered(const float* p) {
+  float4 v;
+  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float4 tex_v4_ordered(cudaTextureObject_t t, int i) {
+  float4 v;
+  asm volatile("tex.1d.v4.f32.s32 {%0, %1, %2, %3}, [%4, {%5}];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(t), "r"(i));
+  return v;
 }
 
 // ---------------------------------------------------------------- staging
@@ -281,6 +299,56 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
     const int32_t* sp = (const int32_t*)((const char*)sv + (sval ? (size_t)CW * sizeof(T) : 0));
     // this lane's steps in the chunk
     const int ns = min(C, len - c * C);
+    if constexpr (sizeof(T) == 4 && EA && EB) {
+      if (a.nother == 2 && a.texB && sval) {
+        // two elements per step, all four rows requested before the first is used
+        constexpr int NA = Row<T, MA>::NV, NB = Row<T, MB>::NV;
+#pragma unroll 1
+        for (int j = 0; j < ns; j += 2) {
+          const int sj0 = j * 32 + lane;
+          const bool has1 = j + 1 < ns;
+          const int sj1 = has1 ? sj0 + 32 : sj0;
+          const T* ra0 = a.F[0] + (int64_t)(int32_t)sw[CW + sj0] * a.ld[0];
+          const T* ra1 = a.F[0] + (int64_t)(int32_t)sw[CW + sj1] * a.ld[0];
+          const int tb0 = (int)(((int64_t)(int32_t)sw[2 * CW + sj0] * a.ld[1] + j0) / 4);
+          const int tb1 = (int)(((int64_t)(int32_t)sw[2 * CW + sj1] * a.ld[1] + j0) / 4);
+          float4 A0[NA], A1[NA], B0[NB], B1[NB];
+#pragma unroll
+          for (int u = 0; u < NA; ++u) A0[u] = ldg_v4_ordered(ra0 + 4 * u);
+#pragma unroll
+          for (int u = 0; u < NB; ++u) B0[u] = tex_v4_ordered(a.texB, tb0 + u);
+#pragma unroll
+          for (int u = 0; u < NA; ++u) A1[u] = ldg_v4_ordered(ra1 + 4 * u);
+#pragma unroll
+          for (int u = 0; u < NB; ++u) B1[u] = tex_v4_ordered(a.texB, tb1 + u);
+          const T v0 = sv[sj0], v1 = has1 ? sv[sj1] : T(0);
+          const uint32_t code0 = sw[sj0], code1 = sw[sj1];
+          T fa0[NA * 4], fa1[NA * 4], fb0[NB * 4], fb1[NB * 4];
+#pragma unroll
+          for (int u = 0; u < NA; ++u) {
+            unpack(A0[u], &fa0[4 * u]);
+            unpack(A1[u], &fa1[4 * u]);
+          }
+#pragma unroll
+          for (int u = 0; u < NB; ++u) {
+            unpack(B0[u], &fb0[4 * u]);
+            unpack(B1[u], &fb1[4 * u]);
+          }
+          if (code0 == cur && code1 == cur) {
+#pragma unroll
+            for (int jj = 0; jj < MB; ++jj) {
+              const T t0 = v0 * fb0[jj], t1 = v1 * fb1[jj];
+#pragma unroll
+              for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(fa1[i], t1, fma(fa0[i], t0, acc[i + MA * jj]));
+            }
+          } else {
+            accumulate(code0, v0, fa0, fb0);
+            if (has1) accumulate(code1, v1, fa1, fb1);
+          }
+        }
+        goto chunk_done;
+      }
+    }
 #pragma unroll 1
     for (int j = 0; j < ns; ++j) {
       const int sj = j * 32 + lane;
@@ -289,6 +357,7 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
       gather(sw, CW, sj, v, fa, fb);
       accumulate(sw[sj], v, fa, fb);
     }
+  chunk_done:
     __syncwarp();
     if (c + 2 < nch) issue_chunk(a, wsm + (c & 1) * sb, CW, wbase, (c + 2) * C, min(C, wlen - (c + 2) * C), lane, sval, sperm);
     cp_commit();
