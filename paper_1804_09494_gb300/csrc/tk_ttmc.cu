@@ -23,6 +23,10 @@
 
 #include "tk_common.cuh"
 
+#ifndef TK_TTMC_NE
+#define TK_TTMC_NE 2  // elements in flight per thread (exact FP32 3-mode tiles)
+#endif
+
 
 namespace {
 
@@ -301,49 +305,61 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
     const int ns = min(C, len - c * C);
     if constexpr (sizeof(T) == 4 && EA && EB) {
       if (a.nother == 2 && a.texB && sval) {
-        // two elements per step, all four rows requested before the first is used
-        constexpr int NA = Row<T, MA>::NV, NB = Row<T, MB>::NV;
+        // NE elements per step, all their rows requested before the first is used
+        constexpr int NA = Row<T, MA>::NV, NB = Row<T, MB>::NV, NE = TK_TTMC_NE;
 #pragma unroll 1
-        for (int j = 0; j < ns; j += 2) {
-          const int sj0 = j * 32 + lane;
-          const bool has1 = j + 1 < ns;
-          const int sj1 = has1 ? sj0 + 32 : sj0;
-          const T* ra0 = a.F[0] + (int64_t)(int32_t)sw[CW + sj0] * a.ld[0];
-          const T* ra1 = a.F[0] + (int64_t)(int32_t)sw[CW + sj1] * a.ld[0];
-          const int tb0 = (int)(((int64_t)(int32_t)sw[2 * CW + sj0] * a.ld[1] + j0) / 4);
-          const int tb1 = (int)(((int64_t)(int32_t)sw[2 * CW + sj1] * a.ld[1] + j0) / 4);
-          float4 A0[NA], A1[NA], B0[NB], B1[NB];
+        for (int j = 0; j < ns; j += NE) {
+          int sjs[NE];
+          bool has[NE];
 #pragma unroll
-          for (int u = 0; u < NA; ++u) A0[u] = ldg_v4_ordered(ra0 + 4 * u);
-#pragma unroll
-          for (int u = 0; u < NB; ++u) B0[u] = tex_v4_ordered(a.texB, tb0 + u);
-#pragma unroll
-          for (int u = 0; u < NA; ++u) A1[u] = ldg_v4_ordered(ra1 + 4 * u);
-#pragma unroll
-          for (int u = 0; u < NB; ++u) B1[u] = tex_v4_ordered(a.texB, tb1 + u);
-          const T v0 = sv[sj0], v1 = has1 ? sv[sj1] : T(0);
-          const uint32_t code0 = sw[sj0], code1 = sw[sj1];
-          T fa0[NA * 4], fa1[NA * 4], fb0[NB * 4], fb1[NB * 4];
-#pragma unroll
-          for (int u = 0; u < NA; ++u) {
-            unpack(A0[u], &fa0[4 * u]);
-            unpack(A1[u], &fa1[4 * u]);
+          for (int e = 0; e < NE; ++e) {
+            has[e] = j + e < ns;
+            sjs[e] = (j + (has[e] ? e : 0)) * 32 + lane;
           }
+          float4 A[NE][NA], B[NE][NB];
 #pragma unroll
-          for (int u = 0; u < NB; ++u) {
-            unpack(B0[u], &fb0[4 * u]);
-            unpack(B1[u], &fb1[4 * u]);
+          for (int e = 0; e < NE; ++e) {
+            const T* ra = a.F[0] + (int64_t)(int32_t)sw[CW + sjs[e]] * a.ld[0];
+            const int tb = (int)(((int64_t)(int32_t)sw[2 * CW + sjs[e]] * a.ld[1] + j0) / 4);
+#pragma unroll
+            for (int u = 0; u < NA; ++u) A[e][u] = ldg_v4_ordered(ra + 4 * u);
+#pragma unroll
+            for (int u = 0; u < NB; ++u) B[e][u] = tex_v4_ordered(a.texB, tb + u);
           }
-          if (code0 == cur && code1 == cur) {
+          T v[NE];
+          uint32_t code[NE];
+          bool same = true;
+#pragma unroll
+          for (int e = 0; e < NE; ++e) {
+            v[e] = has[e] ? sv[sjs[e]] : T(0);
+            code[e] = sw[sjs[e]];
+            same = same && code[e] == cur;
+          }
+          if (same) {
 #pragma unroll
             for (int jj = 0; jj < MB; ++jj) {
-              const T t0 = v0 * fb0[jj], t1 = v1 * fb1[jj];
+              T t[NE];
 #pragma unroll
-              for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(fa1[i], t1, fma(fa0[i], t0, acc[i + MA * jj]));
+              for (int e = 0; e < NE; ++e) t[e] = v[e] * (&B[e][jj / 4].x)[jj % 4];
+#pragma unroll
+              for (int i = 0; i < MA; ++i) {
+                T x = acc[i + MA * jj];
+#pragma unroll
+                for (int e = 0; e < NE; ++e) x = fma((&A[e][i / 4].x)[i % 4], t[e], x);
+                acc[i + MA * jj] = x;
+              }
             }
           } else {
-            accumulate(code0, v0, fa0, fb0);
-            if (has1) accumulate(code1, v1, fa1, fb1);
+#pragma unroll
+            for (int e = 0; e < NE; ++e) {
+              if (!has[e]) break;
+              T fa[NA * 4], fb[NB * 4];
+#pragma unroll
+              for (int u = 0; u < NA; ++u) unpack(A[e][u], &fa[4 * u]);
+#pragma unroll
+              for (int u = 0; u < NB; ++u) unpack(B[e][u], &fb[4 * u]);
+              accumulate(code[e], v[e], fa, fb);
+            }
           }
         }
         goto chunk_done;
