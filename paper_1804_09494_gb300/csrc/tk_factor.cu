@@ -1483,32 +1483,40 @@ __device__ __forceinline__ bool better(const Cand<T>& x, const Cand<T>& y) {
   return x.a > y.a || (x.a == y.a && x.r < y.r);
 }
 
-// U <- U M (row by row) and per-block best (|value|, lowest row) per column.
-template <typename T>
+// U <- U M (row by row) and per-block best (|value|, lowest row) per column;
+// KM >= K is the compile-time bound that keeps the row in registers.
+template <typename T, int KM>
 __global__ void __launch_bounds__(256) k_apply(T* __restrict__ U, int R, int K, const double* __restrict__ M,
                                                double* __restrict__ colbest) {
-  __shared__ T Ms[TK_MAXK][TK_MAXK];
-  __shared__ Cand<T> wbest[8][TK_MAXK];
+  __shared__ T Ms[KM][KM];
+  __shared__ Cand<T> wbest[8][KM];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int i = tid; i < K * K; i += 256) Ms[i / K][i % K] = (T)M[i];
+  for (int i = tid; i < KM * KM; i += 256) {
+    const int r = i / KM, cc = i - r * KM;
+    Ms[r][cc] = (r < K && cc < K) ? (T)M[r * K + cc] : T(0);
+  }
   __syncthreads();
-  Cand<T> best[TK_MAXK];
-  for (int k = 0; k < K; ++k) best[k] = Cand<T>{T(-1), 0x7fffffff, T(0)};
+  Cand<T> best[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) best[k] = Cand<T>{T(-1), 0x7fffffff, T(0)};
   for (int r = blockIdx.x * 256 + tid; r < R; r += gridDim.x * 256) {
-    T u[TK_MAXK], v[TK_MAXK];
-    for (int k = 0; k < K; ++k) u[k] = U[(int64_t)r * K + k];
-    for (int k = 0; k < K; ++k) {
+    T u[KM];
+#pragma unroll
+    for (int k = 0; k < KM; ++k) u[k] = k < K ? U[(int64_t)r * K + k] : T(0);
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
       T s = T(0);
-      for (int j = 0; j <= k; ++j) s = fma(u[j], Ms[j][k], s);
-      v[k] = s;
-    }
-    for (int k = 0; k < K; ++k) {
-      U[(int64_t)r * K + k] = v[k];
-      const Cand<T> c{fabs(v[k]), r, v[k]};
-      if (better(c, best[k])) best[k] = c;
+#pragma unroll
+      for (int j = 0; j <= k; ++j) s = fma(u[j], Ms[j][k], s);  // M upper triangular
+      if (k < K) {
+        U[(int64_t)r * K + k] = s;
+        const Cand<T> c{fabs(s), r, s};
+        if (better(c, best[k])) best[k] = c;
+      }
     }
   }
-  for (int k = 0; k < K; ++k) {
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
     Cand<T> c = best[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1552,13 +1560,19 @@ __global__ void k_signs(const double* colbest, int nblk, int K, double* sign) {
   if (lane == 0) sign[k] = c.v < 0.0 ? -1.0 : 1.0;
 }
 
-template <typename T>
+// F[row_id[r]][k] = sign[k] * U[r][k], thread per row (KM >= K).
+template <typename T, int KM>
 __global__ void k_scatter_rows(const T* __restrict__ U, int R, int K, const int32_t* __restrict__ row_id,
                                const double* __restrict__ sign, T* __restrict__ F, int ldF) {
-  const int64_t total = (int64_t)R * K;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(i / K), k = (int)(i - (int64_t)r * K);
-    F[(int64_t)row_id[r] * ldF + k] = (T)(sign[k] * (double)U[i]);
+  T sg[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) sg[k] = k < K ? (T)sign[k] : T(0);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) {
+    const T* u = U + (int64_t)r * K;
+    T* f = F + (int64_t)row_id[r] * ldF;
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+      if (k < K) f[k] = sg[k] * u[k];
   }
 }
 
@@ -1718,11 +1732,18 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     }
     k_chol_inv<<<1, 1024, 0, s>>>(ws->Cpart, nblk, K, R1, R2, c->err);
     const int nab = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), 2 * sms));
-    k_apply<T><<<nab, 256, 0, s>>>(U, R, K, R2, ws->colbest);
-    k_signs<<<1, 32 * K, 0, s>>>(ws->colbest, nab, K, sign);
-    TK_CUDA(cudaMemsetAsync(F_out, 0, (size_t)c->L[n] * ldF_out * sizeof(T), s));
-    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div((int64_t)R * K, 256), 8 * sms));
-    k_scatter_rows<T><<<gs, 256, 0, s>>>(U, R, K, md.row_id, sign, (T*)F_out, ldF_out);
+    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), 8 * sms));
+    auto tail = [&](auto km) {
+      constexpr int KM = decltype(km)::value;
+      k_apply<T, KM><<<nab, 256, 0, s>>>(U, R, K, R2, ws->colbest);
+      k_signs<<<1, 32 * K, 0, s>>>(ws->colbest, nab, K, sign);
+      TK_CUDA(cudaMemsetAsync(F_out, 0, (size_t)c->L[n] * ldF_out * sizeof(T), s));
+      k_scatter_rows<T, KM><<<gs, 256, 0, s>>>(U, R, K, md.row_id, sign, (T*)F_out, ldF_out);
+    };
+    if (K <= 8) tail(std::integral_constant<int, 8>());
+    else if (K <= 12) tail(std::integral_constant<int, 12>());
+    else if (K <= 16) tail(std::integral_constant<int, 16>());
+    else tail(std::integral_constant<int, 32>());
     TK_CUDA(cudaGetLastError());
     tk_launched(c, PH_BACKPROJ, 8);
     if (sigma_out) TK_CUDA(cudaMemcpyAsync(sigma_out, ws->sigma, K * sizeof(double), cudaMemcpyDeviceToDevice, s));
