@@ -158,8 +158,26 @@ def oracle_sample_seconds(w, sample):
 
 
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_ttmc_fwd_dram_zipf1.1-2Mx1Mx50K-nnz100M.md")
-# the counters hold for these sources (the kernel and the choice of the core's chain)
-TTMC_SOURCES = [os.path.join(ROOT, "paper_1804_09494_gb300", "csrc", f) for f in ("tk_ttmc.cu", "tk_core.cu")]
+CSRC = os.path.join(ROOT, "paper_1804_09494_gb300", "csrc")
+
+
+def source_fingerprints():
+    """sha256 of the TTM-chain kernel file and of the function choosing the
+    core's chain (the launch mix of an invocation): the ncu counters of the
+    traffic profile hold while both are unchanged."""
+    with open(os.path.join(CSRC, "tk_ttmc.cu"), "rb") as f:
+        ttmc = hashlib.sha256(f.read()).hexdigest()
+    with open(os.path.join(CSRC, "tk_core.cu")) as f:
+        src = f.read()
+    i = src.index("int tk_core_mode(")
+    j = src.index("{", i)
+    depth = 0
+    for k in range(j, len(src)):
+        depth += {"{": 1, "}": -1}.get(src[k], 0)
+        if depth == 0:
+            break
+    core_mode_fn = hashlib.sha256(src[i:k + 1].encode()).hexdigest()
+    return {"tk_ttmc.cu": ttmc, "tk_core_mode": core_mode_fn}
 
 
 def ttm_traffic_per_launch(args):
@@ -176,10 +194,9 @@ def ttm_traffic_per_launch(args):
             elif " sha256:" in line:
                 name, h = line.split(" sha256:")
                 sha[name.strip()] = h.strip()
-    for path in TTMC_SOURCES:
-        with open(path, "rb") as f:
-            if sha.get(os.path.basename(path)) != hashlib.sha256(f.read()).hexdigest():
-                return None
+    for name, h in source_fingerprints().items():
+        if sha.get(name) != h:
+            return None
     return val
 
 

@@ -69,12 +69,12 @@ struct FoldInfo {
   int K[TK_MAXN];
 };
 
-// G (first mode fastest) from the split partials, ||G||^2 and the fit; one CTA.
+// G (first mode fastest) from the split partials: 8 lanes per entry, each
+// summing every 8th split in order, combined by a fixed shuffle tree; the
+// entry is written at its folded position.
 template <typename T>
-__global__ void __launch_bounds__(1024) k_core_final(const double* __restrict__ Gpart, int nsplit, FoldInfo fi,
-                                                     double normT2, double* __restrict__ Gd, T* __restrict__ Gout,
-                                                     double* __restrict__ fit_out) {
-  __shared__ double red[33];
+__global__ void __launch_bounds__(256) k_core_fold(const double* __restrict__ Gpart, int nsplit, FoldInfo fi,
+                                                   double* __restrict__ Gd, T* __restrict__ Gout) {
   int stride[TK_MAXN];
   {
     int s = 1;
@@ -84,22 +84,39 @@ __global__ void __launch_bounds__(1024) k_core_final(const double* __restrict__ 
     }
   }
   const int total = fi.Kn * fi.Khat;
-  double g2 = 0.0;
-  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+  const int part = threadIdx.x & 7;
+  const int per_pass = (gridDim.x * blockDim.x) >> 3;
+  for (int base = 0; base < total; base += per_pass) {  // uniform trip count for every lane
+    const int idx0 = base + ((blockIdx.x * blockDim.x + threadIdx.x) >> 3);
+    const bool live = idx0 < total;
+    const int idx = live ? idx0 : 0;
     const int k = idx / fi.Khat, c = idx - k * fi.Khat;
     double s = 0.0;
-    for (int sp = 0; sp < nsplit; ++sp) s += Gpart[((int64_t)sp * fi.Kn + k) * fi.Khat + c];
-    int lin = k * stride[fi.n];
-    int rem = c;
-    for (int m = 0; m < fi.N; ++m) {
-      if (m == fi.n) continue;
-      lin += (rem % fi.K[m]) * stride[m];
-      rem /= fi.K[m];
+    if (live)
+      for (int sp = part; sp < nsplit; sp += 8) s += Gpart[((int64_t)sp * fi.Kn + k) * fi.Khat + c];
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (part == 0 && live) {
+      int lin = k * stride[fi.n];
+      int rem = c;
+      for (int m = 0; m < fi.N; ++m) {
+        if (m == fi.n) continue;
+        lin += (rem % fi.K[m]) * stride[m];
+        rem /= fi.K[m];
+      }
+      Gd[lin] = s;
+      if (Gout) Gout[lin] = (T)s;
     }
-    Gd[lin] = s;
-    if (Gout) Gout[lin] = (T)s;
-    g2 += s * s;
   }
+}
+
+// ||G||^2 (fixed order) and the fit, one CTA.
+__global__ void __launch_bounds__(256) k_core_fit(const double* __restrict__ Gd, int size, double normT2,
+                                                  double* __restrict__ fit_out) {
+  __shared__ double red[33];
+  double g2 = 0.0;
+  for (int i = threadIdx.x; i < size; i += blockDim.x) g2 = fma(Gd[i], Gd[i], g2);
   g2 = block_sum_fixed(g2, red);
   if (threadIdx.x == 0) {
     fit_out[0] = g2;
@@ -155,9 +172,12 @@ void core_impl(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaS
   fi.Kn = K;
   fi.Khat = Khat;
   for (int m = 0; m < c->N; ++m) fi.K[m] = c->K[m];
-  k_core_final<T><<<1, 1024, 0, s>>>(c->Gpart, nsplit, fi, c->normT2, c->Gd, (T*)G_out, c->fit_d);
+  const unsigned gf = (unsigned)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div((int64_t)K * Khat * 8, 256), 4 * c->sm_count));
+  k_core_fold<T><<<gf, 256, 0, s>>>(c->Gpart, nsplit, fi, c->Gd, (T*)G_out);
   TK_CUDA(cudaGetLastError());
-  tk_launched(c, PH_CORE, 2);
+  k_core_fit<<<1, 256, 0, s>>>(c->Gd, (int)c->Gsize, c->normT2, c->fit_d);
+  TK_CUDA(cudaGetLastError());
+  tk_launched(c, PH_CORE, 3);
   tk_phase_end(c, s);
 }
 
