@@ -1,0 +1,120 @@
+"""GPU parity at the full sizes of the other workloads, in the launch
+configuration of the library's defaults:
+  * 4-mode 1M x 500K x 20K x 2K, 500M nonzeros (Zipf 1.2 on modes 1-2, uniform
+    on 3-4), core 10^4 -- TTM-chain rows of every mode (Khat = 1000, ten
+    column groups per element);
+  * 3-mode 500K x 500K x 10K, 20M nonzeros (Zipf 1.1), core 16^3 -- TTM-chain
+    rows and the adjoint.
+The oracle computes sampled rows of eq. (1) from the sampled slices' elements
+alone (a bounded number of elements per mode).  The adjoint is checked through
+identities that hold at any size, because eq. (1) is linear in the values and
+in each factor:  <Z(v'), W> = <v', dval(W)>  and  <Z(F_m -> F'_m), W> =
+<dF_m(W), F'_m>."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import tucker_oracle as O
+from paper_1804_09494_gb300 import synth
+from paper_1804_09494_gb300.tucker import Tucker
+from tests.gpu_cases import TTM_TOL, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+def budget_slices(cnt, E_max, rng, budget):
+    """Slices to check, within `budget` elements in total: first split slices
+    (longer than one bin; the largest below budget/2, then two just longer
+    than one bin), then the lightest slices, then random ones."""
+    nz = np.flatnonzero(cnt > 0)
+    by_size = nz[np.argsort(cnt[nz], kind="stable")]
+    c = cnt[by_size]
+    cand = []
+    j = np.searchsorted(c, budget // 2, side="right") - 1
+    if j >= 0 and c[j] > E_max:
+        cand.append(by_size[j])
+    j = np.searchsorted(c, E_max, side="right")
+    cand += list(by_size[j:j + 2])
+    cand += list(by_size[:6])
+    cand += list(rng.choice(nz, size=min(24, nz.size), replace=False))
+    pick, used = [], 0
+    for s in cand:
+        if s in pick:
+            continue
+        if used + cnt[s] > budget and pick:
+            continue
+        pick.append(s)
+        used += int(cnt[s])
+    return np.unique(np.array(pick, dtype=np.int64))
+
+
+def oracle_rows(L, idx, vals, Fo, n, ids):
+    sel = np.isin(idx[n], ids)
+    sub = idx[:, sel].copy()
+    sub[n] = np.searchsorted(ids, sub[n])
+    Ls = list(L)
+    Ls[n] = len(ids)
+    return O.ttm_chain(tuple(Ls), sub, vals[sel].astype(np.float64), Fo, n)
+
+
+def check_sampled_rows(tk, w, Fd, Fo, n, budget, seed):
+    Z, rid = tk.ttm_chain(n, Fd)
+    torch.cuda.synchronize()
+    rid = rid.cpu().numpy()
+    cnt = np.bincount(w["idx"][n], minlength=w["L"][n])
+    assert np.array_equal(rid, np.flatnonzero(cnt > 0)), "row ids differ from the non-empty slices"
+    ids = budget_slices(cnt, tk.stats(n)["E_max"], np.random.default_rng(seed), budget)
+    rows = np.searchsorted(rid, ids)
+    Zg = Z[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    Zo = oracle_rows(w["L"], w["idx"], w["vals"], Fo, n, ids)
+    assert rel_err(Zg, Zo) <= TTM_TOL["fp32"], (n, rel_err(Zg, Zo))
+    h = int(np.argmax(cnt[ids]))
+    assert rel_err(Zg[h], Zo[h]) <= TTM_TOL["fp32"], (n, int(ids[h]), int(cnt[ids[h]]))
+
+
+def load(name):
+    w = synth.workload(name)
+    F = synth.random_orthonormal_factors(w["L"], w["K"], seed=77)
+    Fo = [f.astype(np.float32).astype(np.float64) for f in F]
+    Fd = [torch.from_numpy(f).float().cuda() for f in Fo]
+    tk = Tucker(torch.from_numpy(w["idx"]).cuda(), torch.from_numpy(w["vals"]).cuda(), w["L"], w["K"], prec="fp32")
+    return w, Fo, Fd, tk
+
+
+def test_fullsize_4mode_500M_ttm_chain_sampled_rows():
+    w, Fo, Fd, tk = load("zipf1.2-1Mx500Kx20Kx2K-nnz500M-k10")
+    try:
+        for n in range(4):
+            check_sampled_rows(tk, w, Fd, Fo, n, budget=600_000, seed=300 + n)
+    finally:
+        tk.close()
+
+
+def test_fullsize_differentiable_20M_k16_rows_and_adjoint_identities():
+    w, Fo, Fd, tk = load("zipf1.1-500Kx500Kx10K-nnz20M-k16")
+    try:
+        g = torch.Generator(device="cuda").manual_seed(5)
+        for n in range(3):
+            check_sampled_rows(tk, w, Fd, Fo, n, budget=1_000_000, seed=400 + n)
+            R, kh = tk.R[n], tk.khat(n)
+            W = torch.randn(R, kh, device="cuda", generator=g)
+            v2 = torch.rand(tk.nnz, device="cuda", generator=g)
+            # values: <Z(v'), W> = <v', dval(W)>
+            Zv, _ = tk.ttm_chain(n, Fd, vals=v2, row_id=False)
+            dF, dval = tk.ttm_chain_backward(n, Fd, W)
+            lhs = float((Zv.double() * W.double()).sum())
+            rhs = float((v2.double() * dval.double()).sum())
+            assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), 1e-30) + 1e-9, (n, lhs, rhs)
+            # factors: <Z(F_m -> F'_m), W> = <dF_m(W), F'_m>
+            for m in range(3):
+                if m == n:
+                    continue
+                Fm2 = torch.randn(w["L"][m], w["K"][m], device="cuda", generator=g)
+                F2 = list(Fd)
+                F2[m] = Fm2
+                Zm, _ = tk.ttm_chain(n, F2, row_id=False)
+                lhs = float((Zm.double() * W.double()).sum())
+                rhs = float((dF[m].double() * Fm2.double()).sum())
+                assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), 1e-30) + 1e-9, (n, m, lhs, rhs)
+    finally:
+        tk.close()
