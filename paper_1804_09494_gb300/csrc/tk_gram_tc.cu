@@ -214,28 +214,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tc(const GramTcArgs a) {
     return true;
   };
 
-  // this thread's (column m, 4-row chunk) pairs of the transposition, the same
-  // for every batch: at most kPairs per thread (Khat * kBatch / 4 <= 1024)
-  constexpr int kPairs = 128 * (kBatch / 4) / kThreads;
+  // Warp 0 only issues copies and MMAs (an MMA issue blocks while the tensor
+  // core is busy, ~0.8 k cycles per batch); warps 1-7 transpose and split.
+  // This thread's (column m, 4-row chunk) pairs of the transposition, the same
+  // for every batch: at most kPairs per thread (Khat * kBatch / 4 <= 1024).
+  constexpr int kXT = kThreads - 32;
+  constexpr int kPairs = (128 * (kBatch / 4) + kXT - 1) / kXT;
   int pm[kPairs], pc[kPairs];
   uint32_t poff[kPairs];
 #pragma unroll
   for (int i = 0; i < kPairs; ++i) {
-    const int pidx = tid + i * kThreads;
-    pm[i] = pidx < Khat * (kBatch / 4) ? pidx % Khat : -1;
-    pc[i] = pidx / Khat;
+    const int pidx = (tid - 32) + i * kXT;
+    pm[i] = (warp > 0 && pidx < Khat * (kBatch / 4)) ? pidx % Khat : -1;
+    pc[i] = pm[i] >= 0 ? pidx / Khat : 0;
     poff[i] = pm[i] >= 0 ? sw128_off(pm[i], 4 * pc[i]) : 0u;
   }
 
   int b = 0;
   for (; b < nb; ++b) {
     const int slot = b % kRaw, st = b & 1;
-    bool okb = mbar_wait_warp(&raw_full[slot], (uint32_t)((b / kRaw) & 1), a.cap);
-    // operand stage st is free once the MMAs of batch b - 2 are done
-    if (okb && b >= 2) okb = mbar_wait_warp(&op_free[st], (uint32_t)(((b - 2) >> 1) & 1), a.cap);
+    bool okb = true;
+    if (warp > 0) {
+      okb = mbar_wait_warp(&raw_full[slot], (uint32_t)((b / kRaw) & 1), a.cap);
+      // operand stage st is free once the MMAs of batch b - 2 are done
+      if (okb && b >= 2) okb = mbar_wait_warp(&op_free[st], (uint32_t)(((b - 2) >> 1) & 1), a.cap);
+    }
     if (!okb) {
       atomicOr(&s_fail, 1);
-    } else {
+    } else if (warp > 0) {
       const int rows = min(kBatch, nrows - b * kBatch);
       const float* rw = raw + slot * rawStage;
       unsigned char* hi = ops + st * 2 * kOpBytes;
