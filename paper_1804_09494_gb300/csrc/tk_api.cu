@@ -272,7 +272,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
       tiles_cap = std::max(tiles_cap, ntiles);
       wp = std::max(wp, (size_t)(2 * c->sm_count + ntiles) * TM * TM);
       const int cb = (int)tk_ceil_div(md.Khat, 128);
-      const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(md.R, 256), tk_ceil_div(4 * c->sm_count, cb)));
+      const int64_t ns = std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(md.R, 64), tk_ceil_div(4 * c->sm_count, cb)));
       gp = std::max(gp, (size_t)ns * c->K[n] * md.Khat);
     }
     const size_t esz = c->esz;

@@ -157,7 +157,7 @@ void core_impl(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaS
   tk_phase_begin(c, PH_CORE, s);
   const int K = c->K[n], Khat = md.Khat, R = md.R;
   const int cb = (int)tk_ceil_div(Khat, 128);
-  int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 256), tk_ceil_div(4 * c->sm_count, cb)));
+  int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(R, 64), tk_ceil_div(4 * c->sm_count, cb)));
   const int rps = (int)tk_ceil_div(R, nsplit);
   dim3 grid(cb, nsplit);
   const T* Z = (const T*)c->Zcore;

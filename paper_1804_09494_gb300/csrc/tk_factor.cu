@@ -664,6 +664,228 @@ __host__ __device__ inline size_t eig_small_smem(int n, int K) {
   return (size_t)2 * K * (K + 1) * sizeof(double) + e * sizeof(T);
 }
 
+// Shared phases of the compact eigensolvers (128 threads): the top-K
+// eigenpairs of the m x m tridiagonal (ta, tb) -- Gershgorin interval,
+// multisection, inverse iteration into tri -- and, after the caller's
+// back-transformation into Xs, modified Gram-Schmidt, the FP64 refinement and
+// the scaled output Vs.
+template <typename T>
+struct EigSmem {
+  T* red;
+  double* lo_s;
+  double* hi_s;
+  T* lam_s;
+  T* inv_sig;
+  int* cnt_s;
+  T* mn_s;
+  T* mx_s;
+  T* b2_s;
+};
+
+template <typename T>
+__device__ void eig_tridiag_topk(const EigArgs<T>& a, const EigSmem<T>& sh, int m, T* ta, T* tb, T* tb2, T* tri,
+                                 T fro, T eps) {
+  const int K = a.K, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NT = kEigSmallThreads, NW = NT / 32;
+  T* red = sh.red;
+  double* lo_s = sh.lo_s;
+  double* hi_s = sh.hi_s;
+  T* lam_s = sh.lam_s;
+  int* cnt_s = sh.cnt_s;
+  T* mn_s = sh.mn_s;
+  T* mx_s = sh.mx_s;
+  T* b2_s = sh.b2_s;
+  // ---- Gershgorin interval and pivot threshold
+  {
+    T mn = T(INFINITY), mx = T(-INFINITY), b2m = T(0);
+    for (int i = tid; i < m; i += NT) {
+      const T bb = tb[i];
+      tb2[i] = bb * bb;
+      const T r = (i > 0 ? fabs(tb[i - 1]) : T(0)) + fabs(bb);
+      mn = fmin(mn, ta[i] - r);
+      mx = fmax(mx, ta[i] + r);
+      b2m = fmax(b2m, bb * bb);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      b2m = fmax(b2m, __shfl_xor_sync(0xffffffffu, b2m, o));
+    }
+    if (lane == 0) {
+      mn_s[wid] = mn;
+      mx_s[wid] = mx;
+      b2_s[wid] = b2m;
+    }
+    __syncthreads();
+    if (tid < K) {
+      T lo = T(INFINITY), hi = T(-INFINITY);
+      for (int i = 0; i < NW; ++i) {
+        lo = fmin(lo, mn_s[i]);
+        hi = fmax(hi, mx_s[i]);
+      }
+      const T pad = T(1e-6) * (hi - lo) + T(10) * eps * fabs(hi) + T(1e-30);
+      lo_s[tid] = (double)(lo - pad);
+      hi_s[tid] = (double)(hi + pad);
+    }
+    if (tid == 0) {
+      T b2 = T(0);
+      for (int i = 0; i < NW; ++i) b2 = fmax(b2, b2_s[i]);
+      red[0] = (sizeof(T) == 4 ? T(1e-30) : T(1e-290)) * fmax(T(1), b2);
+    }
+    __syncthreads();
+  }
+  const T pivmin = red[0];
+  __syncthreads();
+  // ---- multisection for the K largest eigenvalues of T (NT / K sections each)
+  {
+    const int S = NT / K;
+    const double inv_s1 = 1.0 / (double)(S + 1);
+    // shrink by (S + 1) per round down to FP rounding of the interval width
+    const int rounds = (int)ceil((sizeof(T) == 4 ? 24.0 : 53.0) * 0.6931471805599453 / log((double)(S + 1))) + 1;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int k = tid / S, sidx = tid - k * S;
+      if (k < K) {
+        const double step = (hi_s[k] - lo_s[k]) * inv_s1;
+        cnt_s[tid] = sturm_count<T>(ta, tb2, m, (T)(lo_s[k] + step * (double)(sidx + 1)), pivmin);
+      }
+      __syncthreads();
+      if (tid < K) {
+        const int target = m - 1 - tid;  // ascending index of the (tid+1)-th largest eigenvalue
+        const double l0 = lo_s[tid], step = (hi_s[tid] - l0) * inv_s1;
+        double nlo = l0, nhi = hi_s[tid];
+        for (int s2 = 0; s2 < S; ++s2) {
+          if (cnt_s[tid * S + s2] <= target) {
+            nlo = l0 + step * (double)(s2 + 1);
+          } else {
+            nhi = l0 + step * (double)(s2 + 1);
+            break;
+          }
+        }
+        lo_s[tid] = nlo;
+        hi_s[tid] = nhi;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid < K) lam_s[tid] = (T)(0.5 * (lo_s[tid] + hi_s[tid]));
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[2] = clock64();
+  // ---- inverse iteration, one thread per eigenvalue, factors in shared memory
+  for (int k = tid; k < K; k += NT) {
+    T* lu = tri + (size_t)k * 6 * m;
+    T* x = lu + 5 * m;
+    const T tiny = eps * fro + T(1e-30);
+    tri_factor<T>(ta, tb, m, lam_s[k], tiny, lu);
+    for (int i = 0; i < m; ++i) x[i] = hash_unit<T>(101 + k, i);
+    for (int it = 0; it < 3; ++it) {
+      tri_solve<T>(lu, m, x);
+      T nn = T(0);
+      for (int i = 0; i < m; ++i) nn = fma(x[i], x[i], nn);
+      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
+      for (int i = 0; i < m; ++i) x[i] *= inv;
+    }
+  }
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[3] = clock64();
+}
+
+template <typename T>
+__device__ void eig_finish(const EigArgs<T>& a, const EigSmem<T>& sh, int n, T* Xs, double* Cm, double* Rm) {
+  const int K = a.K, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NT = kEigSmallThreads;
+  T* lam_s = sh.lam_s;
+  T* inv_sig = sh.inv_sig;
+  // ---- modified Gram-Schmidt on one warp (separates clustered eigenvalues)
+  if (wid == 0) {
+    for (int k = 0; k < K; ++k) {
+      for (int j = 0; j < k; ++j) {
+        T d = T(0);
+        for (int r = lane; r < n; r += 32) d = fma(Xs[r * K + j], Xs[r * K + k], d);
+        d = warp_allsum(d);
+        for (int r = lane; r < n; r += 32) Xs[r * K + k] -= d * Xs[r * K + j];
+        __syncwarp();
+      }
+      T nn = T(0);
+      for (int r = lane; r < n; r += 32) nn = fma(Xs[r * K + k], Xs[r * K + k], nn);
+      nn = warp_allsum(nn);
+      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
+      for (int r = lane; r < n; r += 32) Xs[r * K + k] *= inv;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[5] = clock64();
+  if (a.polish) {
+    // FP64 refinement: Y = W X, C = Y^T Y, C = R^T R, X' = Y R^-1, sigma_k^2 ~ R_kk
+    for (int idx = tid; idx < n * K; idx += NT) {
+      const int i = idx / K, k = idx - i * K;
+      double s2 = 0.0;
+      const double* wr = a.W + (int64_t)i * n;
+      for (int cc = 0; cc < n; ++cc) s2 = fma(wr[cc], (double)Xs[cc * K + k], s2);
+      a.Y[idx] = s2;
+    }
+    __syncthreads();
+    if (a.clk && tid == 0) a.clk[6] = clock64();
+    for (int pr = tid; pr < K * K; pr += NT) {
+      const int r = pr / K, cc = pr - r * K;
+      if (r <= cc) {
+        double s2 = 0.0;
+        for (int i = 0; i < n; ++i) s2 = fma(a.Y[i * K + r], a.Y[i * K + cc], s2);
+        Cm[(r) * (K + 1) + (cc)] = s2;
+        Cm[(cc) * (K + 1) + (r)] = s2;
+      }
+    }
+    __syncthreads();
+    if (wid == 0) {  // Cholesky C = L L^T (lower, in place) and Ri = L^-T (upper), one warp
+      bool bad = false;
+      for (int j = 0; j < K; ++j) {
+        double d = Cm[(j) * (K + 1) + (j)];
+        if (!(d > 0.0)) bad = true;
+        d = d > 0.0 ? sqrt(d) : 1.0;
+        __syncwarp();
+        if (lane == j) Cm[(j) * (K + 1) + (j)] = d;
+        if (lane > j && lane < K) Cm[(lane) * (K + 1) + (j)] /= d;
+        __syncwarp();
+        if (lane > j && lane < K)
+          for (int k2 = j + 1; k2 <= lane; ++k2) Cm[(lane) * (K + 1) + (k2)] -= Cm[(lane) * (K + 1) + (j)] * Cm[(k2) * (K + 1) + (j)];
+        __syncwarp();
+      }
+      if (bad && lane == 0) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
+      if (lane < K) {
+        for (int i = K - 1; i >= 0; --i) {
+          double s2 = (i == lane) ? 1.0 : 0.0;
+          for (int k2 = i + 1; k2 < K; ++k2) s2 -= Cm[(k2) * (K + 1) + (i)] * Rm[(k2) * (K + 1) + (lane)];
+          Rm[(i) * (K + 1) + (lane)] = (i <= lane) ? s2 / Cm[(i) * (K + 1) + (i)] : 0.0;
+        }
+        a.sigma[lane] = sqrt(fabs(Cm[(lane) * (K + 1) + (lane)]));
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * K; idx += NT) {
+      const int i = idx / K, k = idx - i * K;
+      double s2 = 0.0;
+      for (int j = 0; j <= k; ++j) s2 = fma(a.Y[i * K + j], Rm[(j) * (K + 1) + (k)], s2);
+      a.Vout[idx] = s2;
+    }
+  } else {
+    for (int idx = tid; idx < n * K; idx += NT) a.Vout[idx] = (double)Xs[idx];
+    for (int k = tid; k < K; k += NT) a.sigma[k] = sqrt(fmax((double)lam_s[k], 0.0));
+  }
+  __syncthreads();
+  if (tid < K) {
+    const double sg = a.sigma[tid];
+    const bool ok = sg > 0.0 && isfinite(sg);
+    if (!ok) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
+    inv_sig[tid] = ok ? (T)(1.0 / sg) : T(0);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < n * K; idx += NT) a.Vs[idx] = (T)a.Vout[idx] * inv_sig[idx % K];
+  if (a.clk && tid == 0) a.clk[7] = clock64();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -673,8 +895,7 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
   __shared__ int cnt_s[kEigSmallThreads];
   __shared__ T mn_s[4], mx_s[4], b2_s[4];
   const int n = a.n, K = a.K, tid = threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
-  constexpr int NT = kEigSmallThreads, NW = NT / 32;
+  constexpr int NT = kEigSmallThreads;
   const int m = n, ldq = eig_small_ldq<T>(n);
   // Cholesky factor C and its inverse Ri (refinement), K x (K + 1) row-major
   double* Cm = (double*)smem;
@@ -807,99 +1028,8 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
   __syncthreads();
   if (a.clk && tid == 0) a.clk[1] = clock64();
 
-  // ---- Gershgorin interval and pivot threshold
-  {
-    T mn = T(INFINITY), mx = T(-INFINITY), b2m = T(0);
-    for (int i = tid; i < m; i += NT) {
-      const T bb = tb[i];
-      tb2[i] = bb * bb;
-      const T r = (i > 0 ? fabs(tb[i - 1]) : T(0)) + fabs(bb);
-      mn = fmin(mn, ta[i] - r);
-      mx = fmax(mx, ta[i] + r);
-      b2m = fmax(b2m, bb * bb);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      b2m = fmax(b2m, __shfl_xor_sync(0xffffffffu, b2m, o));
-    }
-    if (lane == 0) {
-      mn_s[wid] = mn;
-      mx_s[wid] = mx;
-      b2_s[wid] = b2m;
-    }
-    __syncthreads();
-    if (tid < K) {
-      T lo = T(INFINITY), hi = T(-INFINITY);
-      for (int i = 0; i < NW; ++i) {
-        lo = fmin(lo, mn_s[i]);
-        hi = fmax(hi, mx_s[i]);
-      }
-      const T pad = T(1e-6) * (hi - lo) + T(10) * eps * fabs(hi) + T(1e-30);
-      lo_s[tid] = (double)(lo - pad);
-      hi_s[tid] = (double)(hi + pad);
-    }
-    if (tid == 0) {
-      T b2 = T(0);
-      for (int i = 0; i < NW; ++i) b2 = fmax(b2, b2_s[i]);
-      red[0] = (sizeof(T) == 4 ? T(1e-30) : T(1e-290)) * fmax(T(1), b2);
-    }
-    __syncthreads();
-  }
-  const T pivmin = red[0];
-  __syncthreads();
-  // ---- multisection for the K largest eigenvalues of T (NT / K sections each)
-  {
-    const int S = NT / K;
-    const double inv_s1 = 1.0 / (double)(S + 1);
-    // shrink by (S + 1) per round down to FP rounding of the interval width
-    const int rounds = (int)ceil((sizeof(T) == 4 ? 24.0 : 53.0) * 0.6931471805599453 / log((double)(S + 1))) + 1;
-    for (int rd = 0; rd < rounds; ++rd) {
-      const int k = tid / S, sidx = tid - k * S;
-      if (k < K) {
-        const double step = (hi_s[k] - lo_s[k]) * inv_s1;
-        cnt_s[tid] = sturm_count<T>(ta, tb2, m, (T)(lo_s[k] + step * (double)(sidx + 1)), pivmin);
-      }
-      __syncthreads();
-      if (tid < K) {
-        const int target = m - 1 - tid;  // ascending index of the (tid+1)-th largest eigenvalue
-        const double l0 = lo_s[tid], step = (hi_s[tid] - l0) * inv_s1;
-        double nlo = l0, nhi = hi_s[tid];
-        for (int s2 = 0; s2 < S; ++s2) {
-          if (cnt_s[tid * S + s2] <= target) {
-            nlo = l0 + step * (double)(s2 + 1);
-          } else {
-            nhi = l0 + step * (double)(s2 + 1);
-            break;
-          }
-        }
-        lo_s[tid] = nlo;
-        hi_s[tid] = nhi;
-      }
-      __syncthreads();
-    }
-  }
-  if (tid < K) lam_s[tid] = (T)(0.5 * (lo_s[tid] + hi_s[tid]));
-  __syncthreads();
-  if (a.clk && tid == 0) a.clk[2] = clock64();
-  // ---- inverse iteration, one thread per eigenvalue, factors in shared memory
-  for (int k = tid; k < K; k += NT) {
-    T* lu = tri + (size_t)k * 6 * m;
-    T* x = lu + 5 * m;
-    const T tiny = eps * fro + T(1e-30);
-    tri_factor<T>(ta, tb, m, lam_s[k], tiny, lu);
-    for (int i = 0; i < m; ++i) x[i] = hash_unit<T>(101 + k, i);
-    for (int it = 0; it < 3; ++it) {
-      tri_solve<T>(lu, m, x);
-      T nn = T(0);
-      for (int i = 0; i < m; ++i) nn = fma(x[i], x[i], nn);
-      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
-      for (int i = 0; i < m; ++i) x[i] *= inv;
-    }
-  }
-  __syncthreads();
-  if (a.clk && tid == 0) a.clk[3] = clock64();
+  const EigSmem<T> sh{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
+  eig_tridiag_topk<T>(a, sh, m, ta, tb, tb2, tri, fro, eps);
   // ---- X = Q S (row r of X from row r of Q)
   for (int idx = tid; idx < n * K; idx += NT) {
     const int r = idx / K, k = idx - r * K;
@@ -916,92 +1046,178 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
   }
   __syncthreads();
   if (a.clk && tid == 0) a.clk[4] = clock64();
-  // ---- modified Gram-Schmidt on one warp (separates clustered eigenvalues)
-  if (wid == 0) {
-    for (int k = 0; k < K; ++k) {
-      for (int j = 0; j < k; ++j) {
-        T d = T(0);
-        for (int r = lane; r < n; r += 32) d = fma(Xs[r * K + j], Xs[r * K + k], d);
-        d = warp_allsum(d);
-        for (int r = lane; r < n; r += 32) Xs[r * K + k] -= d * Xs[r * K + j];
-        __syncwarp();
-      }
-      T nn = T(0);
-      for (int r = lane; r < n; r += 32) nn = fma(Xs[r * K + k], Xs[r * K + k], nn);
-      nn = warp_allsum(nn);
-      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
-      for (int r = lane; r < n; r += 32) Xs[r * K + k] *= inv;
-      __syncwarp();
-    }
+  eig_finish<T>(a, sh, n, Xs, Cm, Rm);
+}
+
+// FP32 form with 16-byte shared-memory traffic, for Khat <= 128 (thread r owns
+// row r): W row-major and the Lanczos basis twice, component-major Q[r][k] for
+// the update w -= Q h and vector-major QT[k][r] for the projections h = Q^T w,
+// so that every inner product reads float4 from its own row and a float4
+// broadcast of the other operand; leading dimensions are odd multiples of 4
+// floats (eight lanes' 16-byte reads fall on distinct banks).  Vectors are
+// padded to a multiple of 4 with zeros, which the Krylov space never touches
+// (W's padding is zero).  The tridiagonal phases, Gram-Schmidt and the FP64
+// refinement are shared with k_eig_small.
+constexpr int kEigV4MaxN = 128;
+
+__host__ __device__ inline int eig_v4_ld(int n) {
+  int l = (n + 3) & ~3;
+  while (l % 8 != 4) l += 4;
+  return l;
+}
+__host__ __device__ inline size_t eig_v4_smem(int n, int K) {
+  const int ld = eig_v4_ld(n), np = (n + 3) & ~3;
+  size_t e = (size_t)3 * n * ld + (size_t)n * K + (size_t)5 * np;
+  if ((size_t)6 * K * n > (size_t)n * ld) e += (size_t)6 * K * n;
+  return (size_t)2 * K * (K + 1) * sizeof(double) + e * sizeof(float);
+}
+
+__global__ void __launch_bounds__(kEigSmallThreads) k_eig_v4(const EigArgs<float> a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ float red[33];
+  __shared__ double lo_s[TK_MAXK], hi_s[TK_MAXK];
+  __shared__ float lam_s[TK_MAXK], inv_sig[TK_MAXK];
+  __shared__ int cnt_s[kEigSmallThreads];
+  __shared__ float mn_s[4], mx_s[4], b2_s[4];
+  const int n = a.n, K = a.K, tid = threadIdx.x;
+  constexpr int NT = kEigSmallThreads;
+  const int m = n, ld = eig_v4_ld(n), np = (n + 3) & ~3, np4 = np / 4;
+  double* Cm = (double*)smem;
+  double* Rm = Cm + K * (K + 1);
+  float* A = (float*)(Rm + K * (K + 1));  // n x ld, row r = W[r][:]
+  float* Q = A + (size_t)n * ld;          // n x ld, Q[r][k]
+  float* QT = Q + (size_t)n * ld;         // m x ld, QT[k][r]
+  float* Xs = QT + (size_t)m * ld;
+  float* ws = Xs + (size_t)n * K;
+  float* hs = ws + np;
+  float* ta = hs + np;
+  float* tb = ta + np;
+  float* tb2 = tb + np;
+  float* tri = ((size_t)6 * K * n <= (size_t)n * ld) ? A : tb2 + np;
+
+  float fro2 = 0.f;
+  for (int idx = tid; idx < n * ld; idx += NT) {
+    const int r = idx / ld, c = idx - r * ld;
+    const float v = c < n ? (float)a.W[(int64_t)r * n + c] : 0.f;
+    A[idx] = v;
+    fro2 = fmaf(v, v, fro2);
+    Q[idx] = 0.f;
+    QT[idx] = 0.f;  // m == n rows
   }
-  __syncthreads();
-  if (a.clk && tid == 0) a.clk[5] = clock64();
-  if (a.polish) {
-    // FP64 refinement: Y = W X, C = Y^T Y, C = R^T R, X' = Y R^-1, sigma_k^2 ~ R_kk
-    for (int idx = tid; idx < n * K; idx += NT) {
-      const int i = idx / K, k = idx - i * K;
-      double s2 = 0.0;
-      const double* wr = a.W + (int64_t)i * n;
-      for (int cc = 0; cc < n; ++cc) s2 = fma(wr[cc], (double)Xs[cc * K + k], s2);
-      a.Y[idx] = s2;
+  for (int i = tid; i < 2 * np; i += NT) ws[i] = 0.f;  // ws and hs, including padding
+  const float fro = sqrtf(block_sum<float>(fro2, red));
+  const float eps = 1.2e-7f;
+  if (a.clk && tid == 0) a.clk[0] = clock64();
+
+  const int r = tid;
+  const bool own = r < n;
+  float w = own ? hash_unit<float>(1, r) : 0.f;
+  {
+    const float inv = 1.f / sqrtf(block_sum<float>(w * w, red));
+    if (own) {
+      QT[r] = w * inv;
+      Q[(size_t)r * ld] = w * inv;
     }
     __syncthreads();
-    if (a.clk && tid == 0) a.clk[6] = clock64();
-    for (int pr = tid; pr < K * K; pr += NT) {
-      const int r = pr / K, cc = pr - r * K;
-      if (r <= cc) {
-        double s2 = 0.0;
-        for (int i = 0; i < n; ++i) s2 = fma(a.Y[i * K + r], a.Y[i * K + cc], s2);
-        Cm[(r) * (K + 1) + (cc)] = s2;
-        Cm[(cc) * (K + 1) + (r)] = s2;
+  }
+  // one classical Gram-Schmidt pass of w against q_0..q_j; returns h_j
+  auto cgs = [&](int j) -> float {
+    if (own) ws[r] = w;
+    __syncthreads();
+    const int jr = (j + 4) & ~3;  // q_0..q_j rounded up to whole float4s
+    if (tid <= j) {
+      const float4* qk = reinterpret_cast<const float4*>(QT + (size_t)tid * ld);
+      const float4* wv = reinterpret_cast<const float4*>(ws);
+      float s0 = 0.f, s1 = 0.f;
+      for (int c4 = 0; c4 < np4; ++c4) {
+        const float4 x = qk[c4], y = wv[c4];
+        s0 = fmaf(x.x, y.x, fmaf(x.y, y.y, s0));
+        s1 = fmaf(x.z, y.z, fmaf(x.w, y.w, s1));
+      }
+      hs[tid] = s0 + s1;
+    } else if (tid < jr) {
+      hs[tid] = 0.f;
+    }
+    __syncthreads();
+    if (own) {
+      const float4* qr = reinterpret_cast<const float4*>(Q + (size_t)r * ld);
+      const float4* hv = reinterpret_cast<const float4*>(hs);
+      float s0 = 0.f, s1 = 0.f;
+      for (int k4 = 0; k4 < jr / 4; ++k4) {
+        const float4 x = qr[k4], y = hv[k4];
+        s0 = fmaf(x.x, y.x, fmaf(x.y, y.y, s0));
+        s1 = fmaf(x.z, y.z, fmaf(x.w, y.w, s1));
+      }
+      w -= s0 + s1;
+    }
+    return hs[j];
+  };
+
+  for (int j = 0; j < m; ++j) {
+    // w = A q_j
+    if (own) {
+      const float4* ar = reinterpret_cast<const float4*>(A + (size_t)r * ld);
+      const float4* qj = reinterpret_cast<const float4*>(QT + (size_t)j * ld);
+      float s0 = 0.f, s1 = 0.f;
+      for (int c4 = 0; c4 < np4; ++c4) {
+        const float4 x = ar[c4], y = qj[c4];
+        s0 = fmaf(x.x, y.x, fmaf(x.y, y.y, s0));
+        s1 = fmaf(x.z, y.z, fmaf(x.w, y.w, s1));
+      }
+      w = s0 + s1;
+    }
+    float al = cgs(j);
+    __syncthreads();  // hs is rewritten by the second pass
+    al += cgs(j);
+    if (tid == 0) ta[j] = al;
+    const float bnorm = sqrtf(block_sum<float>(w * w, red));
+    if (j == m - 1) break;
+    if (bnorm > 100.f * eps * fro) {
+      if (tid == 0) tb[j] = bnorm;
+      const float inv = 1.f / bnorm;
+      if (own) {
+        QT[(size_t)(j + 1) * ld + r] = w * inv;
+        Q[(size_t)r * ld + j + 1] = w * inv;
+      }
+    } else {
+      // invariant subspace: continue with a fresh vector orthogonal to q_0..q_j
+      if (tid == 0) tb[j] = 0.f;
+      w = own ? hash_unit<float>(j + 2, r) : 0.f;
+      cgs(j);
+      __syncthreads();
+      cgs(j);
+      const float n2 = block_sum<float>(w * w, red);
+      const float inv = n2 > 0.f ? 1.f / sqrtf(n2) : 0.f;
+      if (own) {
+        QT[(size_t)(j + 1) * ld + r] = w * inv;
+        Q[(size_t)r * ld + j + 1] = w * inv;
       }
     }
     __syncthreads();
-    if (wid == 0) {  // Cholesky C = L L^T (lower, in place) and Ri = L^-T (upper), one warp
-      bool bad = false;
-      for (int j = 0; j < K; ++j) {
-        double d = Cm[(j) * (K + 1) + (j)];
-        if (!(d > 0.0)) bad = true;
-        d = d > 0.0 ? sqrt(d) : 1.0;
-        __syncwarp();
-        if (lane == j) Cm[(j) * (K + 1) + (j)] = d;
-        if (lane > j && lane < K) Cm[(lane) * (K + 1) + (j)] /= d;
-        __syncwarp();
-        if (lane > j && lane < K)
-          for (int k2 = j + 1; k2 <= lane; ++k2) Cm[(lane) * (K + 1) + (k2)] -= Cm[(lane) * (K + 1) + (j)] * Cm[(k2) * (K + 1) + (j)];
-        __syncwarp();
-      }
-      if (bad && lane == 0) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
-      if (lane < K) {
-        for (int i = K - 1; i >= 0; --i) {
-          double s2 = (i == lane) ? 1.0 : 0.0;
-          for (int k2 = i + 1; k2 < K; ++k2) s2 -= Cm[(k2) * (K + 1) + (i)] * Rm[(k2) * (K + 1) + (lane)];
-          Rm[(i) * (K + 1) + (lane)] = (i <= lane) ? s2 / Cm[(i) * (K + 1) + (i)] : 0.0;
-        }
-        a.sigma[lane] = sqrt(fabs(Cm[(lane) * (K + 1) + (lane)]));
-      }
+  }
+  if (tid == 0) tb[m - 1] = 0.f;
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[1] = clock64();
+
+  const EigSmem<float> sh{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
+  eig_tridiag_topk<float>(a, sh, m, ta, tb, tb2, tri, fro, eps);
+  // ---- X = Q S (row r of X from row r of Q)
+  for (int idx = tid; idx < n * K; idx += NT) {
+    const int rr = idx / K, k = idx - rr * K;
+    const float* x = tri + (size_t)k * 6 * m + 5 * m;
+    const float* qr = Q + (size_t)rr * ld;
+    float s0 = 0.f, s1 = 0.f;
+    int j = 0;
+    for (; j + 1 < m; j += 2) {
+      s0 = fmaf(qr[j], x[j], s0);
+      s1 = fmaf(qr[j + 1], x[j + 1], s1);
     }
-    __syncthreads();
-    for (int idx = tid; idx < n * K; idx += NT) {
-      const int i = idx / K, k = idx - i * K;
-      double s2 = 0.0;
-      for (int j = 0; j <= k; ++j) s2 = fma(a.Y[i * K + j], Rm[(j) * (K + 1) + (k)], s2);
-      a.Vout[idx] = s2;
-    }
-  } else {
-    for (int idx = tid; idx < n * K; idx += NT) a.Vout[idx] = (double)Xs[idx];
-    for (int k = tid; k < K; k += NT) a.sigma[k] = sqrt(fmax((double)lam_s[k], 0.0));
+    if (j < m) s0 = fmaf(qr[j], x[j], s0);
+    Xs[idx] = s0 + s1;
   }
   __syncthreads();
-  if (tid < K) {
-    const double sg = a.sigma[tid];
-    const bool ok = sg > 0.0 && isfinite(sg);
-    if (!ok) atomicOr(a.err, TK_DEV_ERR_NUMERIC);
-    inv_sig[tid] = ok ? (T)(1.0 / sg) : T(0);
-  }
-  __syncthreads();
-  for (int idx = tid; idx < n * K; idx += NT) a.Vs[idx] = (T)a.Vout[idx] * inv_sig[idx % K];
-  if (a.clk && tid == 0) a.clk[7] = clock64();
+  if (a.clk && tid == 0) a.clk[4] = clock64();
+  eig_finish<float>(a, sh, n, Xs, Cm, Rm);
 }
 
 // ------------------------------------------------------------------ back-projection
@@ -1589,6 +1805,7 @@ void setup_eig_attr() {
   if (!done) {
     TK_CUDA(cudaFuncSetAttribute(k_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
     TK_CUDA(cudaFuncSetAttribute(k_eig_small<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmallSmemMax));
+    TK_CUDA(cudaFuncSetAttribute(k_eig_v4, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kEigSmallSmemMax));
     done = true;
   }
 }
@@ -1665,7 +1882,16 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     a.sigma = ws->sigma;
     a.Vs = (T*)ws->Vs;
     a.err = c->err;
-    if (small) k_eig_small<T><<<1, kEigSmallThreads, shm_small, s>>>(a);
+    bool v4 = false;
+    if constexpr (sizeof(T) == 4) {
+      const size_t shm_v4 = eig_v4_smem(Khat, K);
+      if (Khat <= kEigV4MaxN && shm_v4 <= kEigSmallSmemMax) {
+        k_eig_v4<<<1, kEigSmallThreads, shm_v4, s>>>(a);
+        v4 = true;
+      }
+    }
+    if (v4) {
+    } else if (small) k_eig_small<T><<<1, kEigSmallThreads, shm_small, s>>>(a);
     else k_eig<T><<<1, 1024, shm, s>>>(a);
     TK_CUDA(cudaGetLastError());
     tk_launched(c, PH_EIG);
