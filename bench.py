@@ -99,6 +99,25 @@ class Clocks:
 
 
 # ----------------------------------------------------------------- helpers
+def job_time(t_loc, world, device):
+    """The job's timed region: the maximum over ranks of the local one (the job
+    ends when its slowest rank does)."""
+    if world == 1:
+        return t_loc
+    import torch
+    import torch.distributed as dist
+
+    tt = torch.tensor([t_loc], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def per_invocation(t_all, steps, world):
+    """Whole-job seconds per invocation: world ranks each ran `steps`
+    invocations (replicas) within t_all."""
+    return t_all / (steps * world)
+
+
 def dist_info():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -284,15 +303,10 @@ def run_ours(args):
     barrier()
     ck = clocks.stop()
     t_loc = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_loc], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_all = float(tt.item())
-    else:
-        t_all = t_loc
+    t_all = job_time(t_loc, world, dev)
     ph = tk.timings(reset=True)
     launches = int(sum(v[1] for v in ph.values()))
-    s_per_iter = t_all / (args.steps * world)  # whole job: world x steps invocations in t_all
+    s_per_iter = per_invocation(t_all, args.steps, world)
     fit_mixed = fit
 
     # roofline of the dominant kernel (the TTM-chain): algorithmic bytes of the
