@@ -1,7 +1,7 @@
 """Lite distribution scheme along one mode (Section 6.1, Fig. 7), executed
 literally on the CPU.  TEST INFRASTRUCTURE ONLY (see ``oracle/tucker_oracle.py``).
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
 
 * empty slices are dropped before sorting -- they own no element and are
   shared by no bin;
