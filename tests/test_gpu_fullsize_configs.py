@@ -4,7 +4,7 @@ configuration of the library's defaults:
     on 3-4), core 10^4 -- TTM-chain rows of every mode (Khat = 1000, ten
     column groups per element);
   * 3-mode 500K x 500K x 10K, 20M nonzeros (Zipf 1.1), core 16^3 -- TTM-chain
-    rows and the adjoint.
+    rows and the adjoint (FP32 and FP64 contexts).
 The oracle computes sampled rows of eq. (1) from the sampled slices' elements
 alone (a bounded number of elements per mode).  The adjoint is checked through
 identities that hold at any size, because eq. (1) is linear in the values and
@@ -90,31 +90,48 @@ def test_fullsize_4mode_500M_ttm_chain_sampled_rows():
         tk.close()
 
 
+def _adjoint_identities(tk, w, Fd, n, g, dtype, tol):
+    """<Z(v'), W> = <v', dval(W)> and <Z(F_m -> F'_m), W> = <dF_m(W), F'_m>."""
+    R, kh = tk.R[n], tk.khat(n)
+    W = torch.randn(R, kh, device="cuda", generator=g, dtype=torch.float64).to(dtype)
+    v2 = torch.rand(tk.nnz, device="cuda", generator=g, dtype=torch.float64).to(dtype)
+    Zv, _ = tk.ttm_chain(n, Fd, vals=v2, row_id=False)
+    dF, dval = tk.ttm_chain_backward(n, Fd, W)
+    lhs = float((Zv.double() * W.double()).sum())
+    rhs = float((v2.double() * dval.double()).sum())
+    assert abs(lhs - rhs) <= tol * abs(lhs), (n, "values", lhs, rhs)
+    for m in range(3):
+        if m == n:
+            continue
+        Fm2 = torch.randn(w["L"][m], w["K"][m], device="cuda", generator=g, dtype=torch.float64).to(dtype)
+        F2 = list(Fd)
+        F2[m] = Fm2
+        Zm, _ = tk.ttm_chain(n, F2, row_id=False)
+        lhs = float((Zm.double() * W.double()).sum())
+        rhs = float((dF[m].double() * Fm2.double()).sum())
+        assert abs(lhs - rhs) <= tol * abs(lhs), (n, m, lhs, rhs)
+
+
 def test_fullsize_differentiable_20M_k16_rows_and_adjoint_identities():
+    """FP32 context: sampled rows against the oracle; the identities within 1e-3
+    -- dF_m and dval are sums over up to ~3M elements per row taken in FP32 with
+    atomics in a run-dependent order, whose relative rounding is ~sqrt(n) eps32 ~
+    1e-4 and varies from run to run.  FP64 context on the same tensor: the same
+    identities within 1e-9."""
     w, Fo, Fd, tk = load("zipf1.1-500Kx500Kx10K-nnz20M-k16")
     try:
         g = torch.Generator(device="cuda").manual_seed(5)
         for n in range(3):
             check_sampled_rows(tk, w, Fd, Fo, n, budget=1_000_000, seed=400 + n)
-            R, kh = tk.R[n], tk.khat(n)
-            W = torch.randn(R, kh, device="cuda", generator=g)
-            v2 = torch.rand(tk.nnz, device="cuda", generator=g)
-            # values: <Z(v'), W> = <v', dval(W)>
-            Zv, _ = tk.ttm_chain(n, Fd, vals=v2, row_id=False)
-            dF, dval = tk.ttm_chain_backward(n, Fd, W)
-            lhs = float((Zv.double() * W.double()).sum())
-            rhs = float((v2.double() * dval.double()).sum())
-            assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), 1e-30) + 1e-9, (n, lhs, rhs)
-            # factors: <Z(F_m -> F'_m), W> = <dF_m(W), F'_m>
-            for m in range(3):
-                if m == n:
-                    continue
-                Fm2 = torch.randn(w["L"][m], w["K"][m], device="cuda", generator=g)
-                F2 = list(Fd)
-                F2[m] = Fm2
-                Zm, _ = tk.ttm_chain(n, F2, row_id=False)
-                lhs = float((Zm.double() * W.double()).sum())
-                rhs = float((dF[m].double() * Fm2.double()).sum())
-                assert abs(lhs - rhs) <= 1e-4 * max(abs(lhs), 1e-30) + 1e-9, (n, m, lhs, rhs)
+            _adjoint_identities(tk, w, Fd, n, g, torch.float32, 1e-3)
+    finally:
+        tk.close()
+    tk = Tucker(torch.from_numpy(w["idx"]).cuda(), torch.from_numpy(w["vals"]).double().cuda(), w["L"], w["K"],
+                prec="fp64")
+    try:
+        g = torch.Generator(device="cuda").manual_seed(6)
+        Fd64 = [torch.from_numpy(f).cuda() for f in Fo]
+        for n in range(3):
+            _adjoint_identities(tk, w, Fd64, n, g, torch.float64, 1e-9)
     finally:
         tk.close()
