@@ -57,7 +57,9 @@ typedef enum { TUCKER_FP32 = 0, TUCKER_FP64 = 1 } tucker_prec;
 typedef struct {
   int32_t prec;          /* tucker_prec                                                  */
   int32_t P_bins;        /* Lite bins per mode (one TTM-chain thread each); 0 = one per   *
-                          * resident thread, from the device's SM count and occupancy     */
+                          * resident thread of the TTM-chain kernel on all SMs (from the  *
+                          * device's SM count and occupancy), less one CTA, so that a     *
+                          * one-CTA kernel of a concurrent factor update finds room       */
   int32_t gauss_seidel;  /* 0 = Fig. 1 as printed (every mode from the input factors),     *
                           * 1 = textbook HOOI (each mode sees the factors refined so far) */
   int32_t timing;        /* 1 = record CUDA events around every phase (tucker_timings)    */
@@ -181,6 +183,10 @@ tucker_status core(tucker_t t, const void* const* d_F, void* d_G, void* stream);
  *   fit = 1 - sqrt(max(0, ||T||^2 - ||G||^2)) / ||T||   (orthonormal factors).
  * With opts.gauss_seidel = 0 every TTM-chain uses the input factors (Fig. 1 as
  * printed); otherwise mode n uses the factors already refined in this call.
+ * In the first reading the factor update of each mode runs on a stream of the
+ * context, ordered after that mode's TTM-chain on `stream` by an event, and
+ * `stream` waits for all of them before the core is formed: to the caller the
+ * call is ordered on `stream` like a single kernel.
  *   d_F   : host array of N device pointers, factors in (initial) and out (new).
  *   d_G   : output core, prod K values.
  *   h_fit : output fit (host double); may be NULL.  Synchronises when non-NULL.
