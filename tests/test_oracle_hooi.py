@@ -125,19 +125,22 @@ def test_pythagoras_with_dense_residual():
     assert abs(fit - (1 - np.linalg.norm(T - R) / np.linalg.norm(T))) < 1e-12
 
 
-def _dense_hooi(T, F0, iters):
-    """HOOI on the dense tensor: TTM by tensordot, SVD of the dense unfolding."""
+def _dense_hooi(T, F0, iters, in_place=False):
+    """HOOI on the dense tensor: TTM by tensordot, SVD of the dense unfolding.
+    ``in_place`` = textbook (Gauss-Seidel) HOOI: mode n's TTM sees the factors
+    already replaced earlier in the same sweep."""
     N = T.ndim
     F = [f.copy() for f in F0]
     for _ in range(iters):
-        new = []
+        new = [f.copy() for f in F]
         for n in range(N):
+            src = new if in_place else F
             Z = T
             for m in range(N):
                 if m != n:
-                    Z = np.moveaxis(np.tensordot(Z, F[m], axes=([m], [0])), -1, m)
+                    Z = np.moveaxis(np.tensordot(Z, src[m], axes=([m], [0])), -1, m)
             U, _, _ = np.linalg.svd(np.moveaxis(Z, n, 0).reshape(T.shape[n], -1), full_matrices=False)
-            new.append(U[:, : F[n].shape[1]])
+            new[n] = U[:, : F[n].shape[1]]
         F = new
     G = T
     for m in range(N):
@@ -160,6 +163,24 @@ def test_hooi_matches_dense_bruteforce(L, K):
         Gd = np.moveaxis(np.moveaxis(Gd, m, -1) * sgn, -1, m)
     np.testing.assert_allclose(G, Gd.reshape(-1, order="F"), rtol=1e-8, atol=1e-9)
     T = _dense(L, idx, vals)
+    assert abs(fit - (1 - np.sqrt(np.sum(T * T) - np.sum(Gd * Gd)) / np.linalg.norm(T))) < 1e-10
+
+
+@pytest.mark.parametrize("L,K", [((9, 8, 7), (3, 2, 3)), ((6, 5, 4, 5), (2, 3, 2, 2))])
+def test_gauss_seidel_matches_dense_bruteforce(L, K):
+    """The Gauss-Seidel variant against a dense HOOI that replaces each factor
+    in place within the sweep; the Jacobi dense HOOI must land elsewhere, so a
+    variant that silently kept the input factors fails here."""
+    rng = np.random.default_rng(16)
+    idx, vals = _rand_coo(rng, L, int(np.prod(L)) // 3)
+    F0 = [_orth(rng, l, k) for l, k in zip(L, K)]
+    F, G, fit = O.hooi(L, idx, vals, F0, iters=2, variant="gauss_seidel")
+    T = _dense(L, idx, vals)
+    Fd, Gd = _dense_hooi(T, F0, 2, in_place=True)
+    Fj, _ = _dense_hooi(T, F0, 2, in_place=False)
+    for m in range(len(L)):
+        assert O.projector_distance(F[m], Fd[m]) < 1e-9
+    assert max(O.projector_distance(F[m], Fj[m]) for m in range(1, len(L))) > 1e-6
     assert abs(fit - (1 - np.sqrt(np.sum(T * T) - np.sum(Gd * Gd)) / np.linalg.norm(T))) < 1e-10
 
 
