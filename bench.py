@@ -328,7 +328,9 @@ def run_ours(args):
     bytes_per_launch = per_iter_bytes / launches_per_iter
     achieved_gbs = bytes_per_launch / ttm_s_per_launch / 1e9
     traffic = ttm_traffic_per_launch(args)
-    fp32_peak_tflops = 152 * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    # FP32 FMA lanes: 128 per SM on this architecture; SM count from the device
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak_tflops = sms * 128 * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     achieved_tflops = per_iter_flops / launches_per_iter / ttm_s_per_launch / 1e12
 
     # end to end through the public API with pinned host buffers

@@ -47,7 +47,7 @@ typedef enum {
   TUCKER_ERR_OOM = 2,      /* device allocation failed                             */
   TUCKER_ERR_CUDA = 3,     /* a CUDA runtime call failed                           */
   TUCKER_ERR_NUMERIC = 4,  /* numeric breakdown (Cholesky pivot <= 0, non-finite)  */
-  TUCKER_ERR_TIMEOUT = 5,  /* reserved: a bounded device wait ran out              */
+  TUCKER_ERR_TIMEOUT = 5,  /* a bounded device wait ran out (see tucker_opts.wait_cap) */
   TUCKER_ERR_STATE = 6,    /* call not valid for this context                      */
   TUCKER_ERR_INDEX = 7     /* an input coordinate lies outside [0, L[m])           */
 } tucker_status;
@@ -131,8 +131,11 @@ tucker_status tucker_partition(tucker_t t, int mode, int64_t* d_bin_ptr, int32_t
  * The paper has no counterpart; it is a deployment convenience.
  *   - Allocates nothing: the only scratch (the prefix-scan block sums over the
  *     bin lengths) is a static 256 KiB device array that every GPU loading the
- *     library holds until exit; bins are limited accordingly (about 16 million
- *     per mode), larger partitions return TUCKER_ERR_ARG.
+ *     library holds until exit.  It holds one FP64 block sum per 2048 bins
+ *     (plus the sums of those sums), which limits a mode to 67,008,511 bins;
+ *     larger partitions return TUCKER_ERR_ARG.
+ *   - Host threads may make their first call on a device concurrently (the
+ *     address lookup is serialised inside the library).
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before any stream capture.

@@ -1,8 +1,10 @@
 // New factor F~_n = leading K_n left singular vectors of Z_(n) (Fig. 1, "SVD").
 //
 //   W = Z^T Z            Gram over the R_n compact rows (split over rows, FP64 reduction in fixed order)
-//   W V = V Lambda       cyclic-by-rounds Jacobi (Golub & Van Loan 8.5) in one CTA; the FP32
-//                        context polishes the top-K subspace in FP64 (one subspace step + Rayleigh-Ritz)
+//   W V = V Lambda       top-K eigenpairs in one CTA: Lanczos with full re-orthogonalisation,
+//                        eigenvalues of the tridiagonal by multisection (Sturm counts), eigenvectors by
+//                        inverse iteration + modified Gram-Schmidt; the FP32 context polishes the top-K
+//                        subspace in FP64 (one subspace step + Rayleigh-Ritz)
 //   U = Z V Sigma^-1     back-projection
 //   U <- U R^-1 twice    CholeskyQR2 (Gram reductions, Cholesky and inverses in FP64)
 //   signs                column's entry of largest magnitude (lowest slice id on a tie) made positive

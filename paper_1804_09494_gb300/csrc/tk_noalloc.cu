@@ -6,6 +6,9 @@
 // cudaMalloc/cudaFree is not acceptable -- use this variant.  Its only
 // scratch (the block sums of the prefix scan over the bin lengths) lives in
 // the file-scope device array below, so nothing is allocated per call.
+#include <atomic>
+#include <mutex>
+
 #include "tk_common.cuh"
 
 namespace {
@@ -16,24 +19,30 @@ constexpr size_t kNoallocScratchBytes = 256 * 1024;
 static __device__ __align__(256) unsigned char tk_noalloc_scratch[kNoallocScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void* g_scratch_addr[kMaxDevices] = {};
+std::atomic<void*> g_scratch_addr[kMaxDevices] = {};
+std::mutex g_scratch_mutex;
 
 // The array's name is a host-side stand-in in host code; the device address
-// is looked up once per device, with that device current.
+// is looked up once per device, with that device current.  Host threads that
+// make their first call on the same device at the same time are serialised by
+// the mutex; later calls only read the atomic entry.
 void* scratch_for_current_device() {
   int dev = 0;
   TK_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) tk_throw(TUCKER_ERR_STATE, "device ordinal out of range for the static scratch table");
-  if (!g_scratch_addr[dev]) {
-    void* ptr = nullptr;
+  void* ptr = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (ptr) return ptr;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  ptr = g_scratch_addr[dev].load(std::memory_order_relaxed);
+  if (!ptr) {
     const cudaError_t e = cudaGetSymbolAddress(&ptr, tk_noalloc_scratch);
     if (e != cudaSuccess || !ptr) {
       cudaGetLastError();
       tk_throw(TUCKER_ERR_CUDA, std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e));
     }
-    g_scratch_addr[dev] = ptr;
+    g_scratch_addr[dev].store(ptr, std::memory_order_release);
   }
-  return g_scratch_addr[dev];
+  return ptr;
 }
 
 struct Call {

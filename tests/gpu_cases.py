@@ -12,6 +12,12 @@ NP = {"fp32": np.float32, "fp64": np.float64}
 # relative Frobenius tolerance of the TTM-chain: FP32 per the method's
 # acceptance bound; FP64 from ~1e3 rounding steps of 1.1e-16
 TTM_TOL = {"fp32": 1e-5, "fp64": 1e-12}
+# per-row bound: max over rows of ||Z_r - Zo_r|| / ||Zo_r||.  A row sums at most
+# one bin's worth of elements (<= ceil(nnz/P)) sequentially in the working
+# precision, a relative rounding error of about eps * sqrt(n/2) (2e-6 in FP32
+# at n = 2,600); dropping or doubling one element of a row of n elements moves
+# it by about 1/sqrt(n) (2e-3 at n = 2e5), far above both bounds.
+ROW_TOL = {"fp32": 5e-5, "fp64": 1e-11}
 
 
 def case(L, nnz, zipf=None, values="uniform", seed=0):
@@ -37,6 +43,16 @@ def rel_err(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def row_rel_err(a, b):
+    """max over rows of ||a_r - b_r|| / ||b_r|| (rows of b that are exactly zero
+    must be exactly zero in a)."""
+    na = np.linalg.norm(a - b, axis=1)
+    nb = np.linalg.norm(b, axis=1)
+    zero = nb == 0
+    assert not np.any(na[zero] > 0), "a row that must be zero is not"
+    return float(np.max(na[~zero] / nb[~zero])) if np.any(~zero) else 0.0
+
+
 def check_ttm(tk, c, Fd, Fo, n, prec, vals=None, vals_np=None):
     Z, rid = tk.ttm_chain(n, Fd, vals=vals)
     torch.cuda.synchronize()
@@ -45,6 +61,9 @@ def check_ttm(tk, c, Fd, Fo, n, prec, vals=None, vals_np=None):
     cnt = np.bincount(c["idx"][n], minlength=c["L"][n])
     rid = rid.cpu().numpy()
     assert np.array_equal(rid, np.flatnonzero(cnt > 0)), "row ids differ from the non-empty slices"
-    err = rel_err(Z.double().cpu().numpy(), Zo[rid])
+    Zg = Z.double().cpu().numpy()
+    err = rel_err(Zg, Zo[rid])
     assert err <= TTM_TOL[prec], (n, err)
+    rerr = row_rel_err(Zg, Zo[rid])
+    assert rerr <= ROW_TOL[prec], (n, "row", rerr)
     return Z, rid, Zo, err

@@ -17,7 +17,7 @@ import torch
 from oracle import tucker_oracle as O
 from paper_1804_09494_gb300 import synth
 from paper_1804_09494_gb300.tucker import Tucker
-from tests.gpu_cases import TTM_TOL, rel_err
+from tests.gpu_cases import ROW_TOL, TTM_TOL, rel_err, row_rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -68,6 +68,7 @@ def check_sampled_rows(tk, w, Fd, Fo, n, budget, seed):
     Zg = Z[torch.from_numpy(rows).cuda()].double().cpu().numpy()
     Zo = oracle_rows(w["L"], w["idx"], w["vals"], Fo, n, ids)
     assert rel_err(Zg, Zo) <= TTM_TOL["fp32"], (n, rel_err(Zg, Zo))
+    assert row_rel_err(Zg, Zo) <= ROW_TOL["fp32"], (n, "row", row_rel_err(Zg, Zo))
     h = int(np.argmax(cnt[ids]))
     assert rel_err(Zg[h], Zo[h]) <= TTM_TOL["fp32"], (n, int(ids[h]), int(cnt[ids[h]]))
 
