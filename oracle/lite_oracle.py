@@ -8,7 +8,12 @@ Readings of points the paper leaves open:
 * slices are sorted by (cardinality, slice id) ascending (the paper only says
   "increasing order of cardinality");
 * "Select any g elements" takes the first g remaining elements of the slice in
-  original COO order;
+  its *listing order*: the slice's elements ordered by the popularity rank of
+  their coordinate along the fiber mode f(n) -- the other mode with the fewest
+  slices (smallest L_m, lowest m on a tie); rank 0 is that mode's largest slice,
+  ties by lower slice id -- and then by original COO position.  The paper leaves
+  the choice free; this order lists each mode-n fiber's elements together and
+  every bin's elements from the most to the least frequent fiber coordinate;
 * both stages stop when the slices run out (the printed loops have no bound on
   t); stage 2 always finishes because P * ceil(|E|/P) >= |E|;
 * the bin index follows the pseudocode's counter (p starts at 0, advances
@@ -16,7 +21,7 @@ Readings of points the paper leaves open:
 
 A bin's contents are kept as a list of *pieces* (slice id, first rank j0 within
 the slice, count) in the order the pseudocode assigns them; the elements of a
-piece are the slice's elements of original-order rank j0 .. j0+count-1.
+piece are the slice's elements of listing-order rank j0 .. j0+count-1.
 """
 from __future__ import annotations
 
@@ -76,27 +81,48 @@ def lite_pieces(cnt, P):
     return {"pieces": pieces, "t_hat": t_hat, "order": order, "limit": limit}
 
 
-def slice_members(idx_n, L_n):
-    """Elements of every slice in original COO order: returns (elems, start)
+def fiber_mode(L, n):
+    """f(n): the mode other than n with the fewest slices (smallest L_m,
+    lowest m on a tie)."""
+    return min((m for m in range(len(L)) if m != n), key=lambda m: (int(L[m]), m))
+
+
+def popularity_rank(idx_m, L_m):
+    """rank[l] = position of slice l of a mode when its slices are listed by
+    decreasing cardinality, ties by increasing slice id (empty slices last)."""
+    cnt = np.bincount(np.asarray(idx_m, dtype=np.int64), minlength=int(L_m))
+    order = sorted(range(int(L_m)), key=lambda l: (-int(cnt[l]), l))
+    rank = np.empty(int(L_m), dtype=np.int64)
+    rank[np.array(order, dtype=np.int64)] = np.arange(int(L_m))
+    return rank
+
+
+def slice_members(idx, L, n):
+    """Elements of every mode-n slice in listing order (popularity rank of the
+    fiber-mode coordinate, then original position): returns (elems, start)
     such that slice l's elements are elems[start[l]:start[l+1]]."""
-    idx_n = np.asarray(idx_n, dtype=np.int64)
-    elems = np.argsort(idx_n, kind="stable")
-    cnt = np.bincount(idx_n, minlength=L_n)
-    start = np.zeros(L_n + 1, dtype=np.int64)
+    idx = [np.asarray(x, dtype=np.int64) for x in idx]
+    f = fiber_mode(L, n)
+    key = popularity_rank(idx[f], L[f])[idx[f]]
+    nnz = len(idx[n])
+    elems = np.lexsort((np.arange(nnz), key, idx[n]))
+    cnt = np.bincount(idx[n], minlength=int(L[n]))
+    start = np.zeros(int(L[n]) + 1, dtype=np.int64)
     np.cumsum(cnt, out=start[1:])
     return elems, start
 
 
-def lite_assignment(idx_n, L_n, P):
-    """Element-level Lite partition along a mode.
+def lite_assignment(idx, L, n, P):
+    """Element-level Lite partition along mode n of a COO tensor with
+    coordinates ``idx`` (N arrays) and mode lengths ``L``.
 
     Returns (bin_ptr, perm, info): bin p owns the original element ids
     perm[bin_ptr[p]:bin_ptr[p+1]], listed piece by piece in assignment order and,
-    within a piece, in original order.  ``info`` is the dict of ``lite_pieces``.
+    within a piece, in listing order.  ``info`` is the dict of ``lite_pieces``.
     """
-    cnt = np.bincount(np.asarray(idx_n, dtype=np.int64), minlength=L_n)
+    cnt = np.bincount(np.asarray(idx[n], dtype=np.int64), minlength=int(L[n]))
     info = lite_pieces(cnt, P)
-    elems, start = slice_members(idx_n, L_n)
+    elems, start = slice_members(idx, L, n)
     bin_ptr = np.zeros(P + 1, dtype=np.int64)
     out = []
     for p in range(P):

@@ -28,7 +28,7 @@ def test_partition_bit_exact(name, L, nnz, zipf, K, P):
         st = tk.stats(n)
         bin_ptr, perm = tk.partition(n)
         torch.cuda.synchronize()
-        ob, operm, info = LO.lite_assignment(c["idx"][n], L[n], st["P"])
+        ob, operm, info = LO.lite_assignment(c["idx"], L, n, st["P"])
         assert np.array_equal(bin_ptr.cpu().numpy(), ob), (n, "bin sizes")
         assert np.array_equal(perm.cpu().numpy().astype(np.int64), operm), (n, "element assignment")
         m = LO.metrics(info["pieces"])
@@ -65,6 +65,6 @@ def test_partition_fig6_worked_example():
         assert np.array_equal(got, want), (p, got, want)
     st = tk.stats(0)
     assert (st["E_max"], st["R_sum"], st["R_max"]) == (int(d["E_max"][0]), int(d["R_sum"][0]), int(d["R_max"][0]))
-    ob, operm, _ = LO.lite_assignment(idx[0], len(sizes), P)
+    ob, operm, _ = LO.lite_assignment(idx, c["L"], 0, P)
     assert np.array_equal(bin_ptr, ob) and np.array_equal(perm.astype(np.int64), operm)
     tk.close()

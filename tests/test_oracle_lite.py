@@ -131,15 +131,29 @@ def test_framework_example_metrics():
     assert m["E_max"] == 3
 
 
-def test_assignment_lists_elements_in_original_order():
+def test_assignment_lists_elements_in_listing_order():
+    """Pieces tile each slice's elements in listing order: by the popularity
+    rank of the fiber-mode coordinate (mode 2 here, the shortest other mode:
+    its largest slice first, ties by lower id), then original position --
+    checked against an order built by brute force from the definition."""
     rng = np.random.default_rng(7)
-    idx = rng.integers(0, 30, size=500)
-    bin_ptr, perm, info = LO.lite_assignment(idx, 30, 9)
+    L = (30, 12, 5)
+    idx = np.stack([rng.integers(0, l, size=500) for l in L])
+    assert LO.fiber_mode(L, 0) == 2 and LO.fiber_mode(L, 2) == 1 and LO.fiber_mode((4, 3, 3), 0) == 1
+    cnt2 = np.bincount(idx[2], minlength=5)
+    by_pop = sorted(range(5), key=lambda l: (-cnt2[l], l))
+    bin_ptr, perm, info = LO.lite_assignment(idx, L, 0, 9)
     assert sorted(perm.tolist()) == list(range(500))
     for p in range(9):
         seg = perm[bin_ptr[p]: bin_ptr[p + 1]]
         assert len(seg) <= info["limit"]
         for (s, j0, c) in info["pieces"][p]:
-            mem = np.flatnonzero(idx == s)[j0: j0 + c]
-            assert np.array_equal(seg[:c], mem)
+            mem = [e for l2 in by_pop for e in range(500) if idx[0][e] == s and idx[2][e] == l2]
+            assert np.array_equal(seg[:c], np.array(mem[j0: j0 + c]))
             seg = seg[c:]
+
+
+def test_popularity_rank_definition():
+    idx = np.array([3, 1, 3, 0, 1, 3, 4])
+    # sizes: 0:1, 1:2, 2:0, 3:3, 4:1 -> order 3, 1, 0, 4, 2
+    np.testing.assert_array_equal(LO.popularity_rank(idx, 5), [2, 1, 4, 0, 3])
