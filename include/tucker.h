@@ -54,6 +54,19 @@ typedef enum {
 
 typedef enum { TUCKER_FP32 = 0, TUCKER_FP64 = 1 } tucker_prec;
 
+/*
+ * Device-memory callbacks.  alloc returns `bytes` bytes of device memory
+ * (256-byte aligned) that stay valid until free is called on them, or NULL
+ * when it cannot; it is called on the host thread of tucker_init (context
+ * memory and init temporaries), of tucker_partition (a scan temporary) and of
+ * ttm_chain_backward (the adjoint's workspace, on its first call).  `stream` is the stream of that call: the
+ * library orders its own use of the memory on that stream and on internal
+ * streams, and synchronises the device before calling free, so an allocator
+ * that reuses freed memory on `stream` (a caching allocator) is safe.
+ */
+typedef void* (*tucker_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*tucker_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
 typedef struct {
   int32_t prec;          /* tucker_prec                                                  */
   int32_t P_bins;        /* Lite bins per mode (one TTM-chain thread each); 0 = one per   *
@@ -70,10 +83,15 @@ typedef struct {
                           * -1 = abandon every such wait at once (fault injection: runs   *
                           * the timeout path -- copies and MMAs in flight are still       *
                           * awaited -- with no stuck wait)                                */
-  int32_t reserved[7];   /* must be zero                                                  */
+  int32_t reserved0;     /* must be zero                                                  */
+  tucker_alloc_fn alloc; /* NULL: the library calls cudaMalloc / cudaFree itself          */
+  tucker_free_fn free;   /* must be non-NULL exactly when alloc is                        */
+  void* alloc_user;      /* passed to alloc and free                                      */
+  int32_t reserved[4];   /* must be zero                                                  */
 } tucker_opts;
 
-/* Fills *opts with the defaults (FP32, automatic P, Jacobi reading, no timing). */
+/* Fills *opts with the defaults (FP32, automatic P, Jacobi reading, no timing,
+ * cudaMalloc). */
 void tucker_default_opts(tucker_opts* opts);
 
 /*
@@ -91,6 +109,8 @@ void tucker_default_opts(tucker_opts* opts);
  *   d_idx    : host array of N device pointers; d_idx[m] holds nnz int32 coordinates.
  *   d_val    : nnz values (float or double per opts->prec).
  *   opts     : NULL = defaults.
+ * Every byte of device memory the context owns, and every temporary of this
+ * call, comes from opts->alloc when it is set (cudaMalloc otherwise).
  * Synchronises `stream`.  Returns TUCKER_ERR_INDEX if a coordinate is out of
  * range, TUCKER_ERR_ARG for bad sizes or non-finite values, TUCKER_ERR_OOM if
  * the workspace does not fit.  On error *out is NULL.
@@ -99,7 +119,8 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
                           const int32_t* const* d_idx, const void* d_val, const tucker_opts* opts,
                           void* stream);
 
-/* Releases the context and all library-owned device memory (synchronises). */
+/* Releases the context and all library-owned device memory (synchronises the
+ * device, then returns the memory through opts->free or cudaFree). */
 void tucker_destroy(tucker_t t);
 
 /* Message of the last error on this context (or of the last failed init when t is NULL). */

@@ -58,7 +58,7 @@ void release(tucker_ctx* c) {
     if (c->texFa[m]) cudaDestroyTextureObject(c->texFa[m]);
     if (c->texFb[m]) cudaDestroyTextureObject(c->texFb[m]);
   }
-  for (void* p : c->allocs) cudaFree(p);
+  for (auto& a : c->allocs) tk_dev_free(c, a.first, a.second);
   c->allocs.clear();
   if (c->timing)
     for (int i = 0; i < 2 * kEvPairs; ++i) cudaEventDestroy(c->ev[i]);
@@ -90,7 +90,7 @@ void copy_in_factors(tucker_ctx* c, const void* const* d_F, int skip, cudaStream
   for (int m = 0; m < c->N; ++m) {
     if (m == skip) continue;
     if (!d_F || !d_F[m]) tk_throw(TUCKER_ERR_ARG, "factor pointer for mode " + std::to_string(m) + " is NULL");
-    tk_copy_factor(c, d_F[m], c->K[m], c->Fa[m], c->ldF[m], c->L[m], c->K[m], s);
+    tk_copy_factor(c, d_F[m], c->K[m], c->Fa[m], c->ldF[m], c->L[m], c->K[m], c->relabel[m], nullptr, s);
   }
 }
 
@@ -135,15 +135,36 @@ void tk_check_cuda(cudaError_t e, const char* what) {
   }
 }
 
-void* tk_alloc(tucker_ctx* c, size_t bytes) {
-  void* p = nullptr;
+void* tk_dev_alloc(tucker_ctx* c, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  void* p = nullptr;
+  if (c->alloc_fn) {
+    p = c->alloc_fn(bytes, (void*)c->alloc_stream, c->alloc_user);
+    if (!p) tk_throw(TUCKER_ERR_OOM, "the caller's allocator returned NULL for " + std::to_string(bytes) + " bytes");
+    if ((uintptr_t)p % 256 != 0) {
+      c->free_fn(p, bytes, (void*)c->alloc_stream, c->alloc_user);
+      tk_throw(TUCKER_ERR_ARG, "the caller's allocator returned memory that is not 256-byte aligned");
+    }
+    return p;
+  }
   const cudaError_t e = cudaMalloc(&p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     tk_throw(TUCKER_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
   }
-  c->allocs.push_back(p);
+  return p;
+}
+
+void tk_dev_free(tucker_ctx* c, void* p, size_t bytes) {
+  if (!p) return;
+  if (bytes == 0) bytes = 16;
+  if (c->free_fn) c->free_fn(p, bytes, (void*)c->alloc_stream, c->alloc_user);
+  else cudaFree(p);
+}
+
+void* tk_alloc(tucker_ctx* c, size_t bytes) {
+  void* p = tk_dev_alloc(c, bytes);
+  c->allocs.emplace_back(p, bytes == 0 ? 16 : bytes);
   c->bytes += (int64_t)bytes;
   return p;
 }
@@ -198,8 +219,10 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     if (o.prec != TUCKER_FP32 && o.prec != TUCKER_FP64) tk_throw(TUCKER_ERR_ARG, "unknown precision");
     if (o.P_bins < 0) tk_throw(TUCKER_ERR_ARG, "P_bins must be >= 0");
     if (o.wait_cap < -1) tk_throw(TUCKER_ERR_ARG, "wait_cap must be >= -1");
-    for (int i = 0; i < 7; ++i)
+    if (o.reserved0) tk_throw(TUCKER_ERR_ARG, "reserved option fields must be zero");
+    for (int i = 0; i < 4; ++i)
       if (o.reserved[i]) tk_throw(TUCKER_ERR_ARG, "reserved option fields must be zero");
+    if ((o.alloc == nullptr) != (o.free == nullptr)) tk_throw(TUCKER_ERR_ARG, "alloc and free must be set together");
     for (int m = 0; m < N; ++m) {
       if (L[m] < 1 || L[m] >= ((int64_t)1 << 31) - 1) tk_throw(TUCKER_ERR_ARG, "mode length out of range");
       if (K[m] < 1 || K[m] > TK_MAXK || (int64_t)K[m] > L[m])
@@ -215,6 +238,10 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     c->timing = o.timing != 0;
     c->wait_cap = o.wait_cap;
     c->sm_count = tk_sm_count();
+    c->alloc_fn = o.alloc;
+    c->free_fn = o.free;
+    c->alloc_user = o.alloc_user;
+    c->alloc_stream = (cudaStream_t)stream;
     for (int m = 0; m < N; ++m) {
       c->L[m] = L[m];
       c->K[m] = K[m];
@@ -237,6 +264,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     c->normT2 = tk_norm2(c, d_val, nnz, s);
     check_device_error(c, s);
     if (!(c->normT2 > 0.0)) tk_throw(TUCKER_ERR_ARG, "the tensor has zero norm");
+    tk_relabel_modes(c, d_idx, s);
 
     for (int n = 0; n < N; ++n) {
       const int G = tk_ttmc_groups(c, n);
@@ -352,7 +380,7 @@ tucker_status factor_update(tucker_t t, int mode, const void* d_Z, void* d_F_out
     check_ctx(t);
     check_mode(t, mode);
     if (!d_Z || !d_F_out) tk_throw(TUCKER_ERR_ARG, "NULL buffer");
-    tk_factor_update(t, mode, d_Z, d_F_out, t->K[mode], d_sigma, (cudaStream_t)stream);
+    tk_factor_update(t, mode, d_Z, d_F_out, t->K[mode], t->mode[mode].row_id, d_sigma, (cudaStream_t)stream);
   });
 }
 
@@ -377,7 +405,7 @@ tucker_status hooi_iter(tucker_t t, void* const* d_F, void* d_G, double* h_fit, 
         void* src[TK_MAXN];
         for (int m = 0; m < t->N; ++m) src[m] = m < n ? t->Fb[m] : t->Fa[m];
         tk_ttmc_forward(t, n, src, t->ldF, nullptr, t->Zm[n], s);
-        tk_factor_update(t, n, t->Zm[n], t->Fb[n], t->ldF[n], nullptr, s);
+        tk_factor_update(t, n, t->Zm[n], t->Fb[n], t->ldF[n], t->mode[n].frow, nullptr, s);
       }
     } else {
       // Fig. 1 as printed: every TTM-chain reads the input factors, so the
@@ -391,7 +419,7 @@ tucker_status hooi_iter(tucker_t t, void* const* d_F, void* d_G, double* h_fit, 
         tk_ttmc_forward(t, n, t->Fa, t->ldF, nullptr, t->Zm[n], s);
         TK_CUDA(cudaEventRecord(t->ev_ttm[n], s));
         TK_CUDA(cudaStreamWaitEvent(t->aux[n], t->ev_ttm[n], 0));
-        tk_factor_update(t, n, t->Zm[n], t->Fb[n], t->ldF[n], nullptr, t->aux[n]);
+        tk_factor_update(t, n, t->Zm[n], t->Fb[n], t->ldF[n], t->mode[n].frow, nullptr, t->aux[n]);
         TK_CUDA(cudaEventRecord(t->ev_fu[n], t->aux[n]));
       }
       for (int n = 0; n < t->N; ++n)
@@ -399,7 +427,8 @@ tucker_status hooi_iter(tucker_t t, void* const* d_F, void* d_G, double* h_fit, 
       tk_core(t, t->Fb, t->ldF, d_G, s, t->ev_fu[nc]);
     }
     if (t->gauss_seidel) tk_core(t, t->Fb, t->ldF, d_G, s);
-    for (int m = 0; m < t->N; ++m) tk_copy_factor(t, t->Fb[m], t->ldF[m], d_F[m], t->K[m], t->L[m], t->K[m], s);
+    for (int m = 0; m < t->N; ++m)
+      tk_copy_factor(t, t->Fb[m], t->ldF[m], d_F[m], t->K[m], t->L[m], t->K[m], nullptr, t->relabel[m], s);
     if (h_fit) {
       TK_CUDA(cudaMemcpyAsync(h_fit, t->fit_d + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
       check_device_error(t, s);

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/tucker.h"
@@ -54,6 +55,7 @@ struct tk_mode {
   int32_t* perm = nullptr;
   int32_t* bin_len = nullptr;
   int32_t* row_id = nullptr;    // R slice ids
+  int32_t* frow = nullptr;      // R internal factor rows: relabel[n][row_id[r]]
   // split-slice fix-up tables
   int32_t* split_row = nullptr;   // nsplit compact rows
   int32_t* split_bhead = nullptr; // nsplit
@@ -103,9 +105,23 @@ struct tucker_ctx {
   int sm_count = 0;
   double normT2 = 0.0;
   tk_mode mode[TK_MAXN];
-  // library-owned device memory (everything allocated at init)
-  std::vector<void*> allocs;
+  // library-owned device memory (everything allocated at init, plus the
+  // adjoint's workspace on its first use), from the caller's callbacks or cudaMalloc
+  std::vector<std::pair<void*, size_t>> allocs;
   int64_t bytes = 0;
+  tucker_alloc_fn alloc_fn = nullptr;
+  tucker_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
+  cudaStream_t alloc_stream = nullptr;
+  // Row labels.  Every mode's slices are relabelled by popularity: relabel[m][l]
+  // = rank of slice l when the slices of mode m are listed by decreasing
+  // cardinality (ties by lower id, empty slices last); unlabel[m] is the
+  // inverse.  The permuted copies store relabelled coordinates and the factor
+  // buffers Fa/Fb hold row relabel[m][l] = row l of the caller's factor, so
+  // the most gathered rows sit together at the start of each buffer.
+  int32_t* relabel[TK_MAXN] = {};
+  int32_t* unlabel[TK_MAXN] = {};
+  int fiber[TK_MAXN] = {};  // f(n): the other mode with the smallest length (lowest index on a tie)
   // factor buffers, padded leading dimension ldF[m]
   int ldF[TK_MAXN] = {};
   void* Fa[TK_MAXN] = {};   // current factors
@@ -126,6 +142,13 @@ struct tucker_ctx {
   cudaStream_t aux[TK_MAXN] = {};
   cudaEvent_t ev_ttm[TK_MAXN] = {};
   cudaEvent_t ev_fu[TK_MAXN] = {};
+  // adjoint workspace (allocated by the first ttm_chain_backward call)
+  bool bwd_ready = false;
+  int32_t* bwd_pos[TK_MAXN] = {};  // nnz: slot of element e in mode m's copy
+  void* bwd_X = nullptr;           // max_m cap_m * K_m: per-slot contributions to dF_m
+  void* bwd_Zc = nullptr;          // max_m R_m * K_m: compact dF_m
+  void* bwd_Zp = nullptr;          // max_m 2 * Pa_m * K_m: split-piece partials
+  double* bwd_Zch = nullptr;       // max_m nchunks_m * K_m: fix-up chunk sums
   double* Gpart = nullptr;  // core partials
   double* Gd = nullptr;     // core (double) prod K
   double* fit_d = nullptr;  // [0] = ||G||^2, [1] = fit
@@ -145,6 +168,10 @@ struct tucker_ctx {
 void tk_throw(tucker_status code, const std::string& msg);
 void tk_check_cuda(cudaError_t e, const char* what);
 void* tk_alloc(tucker_ctx* c, size_t bytes);
+// temporary device memory through the context's callbacks (or cudaMalloc);
+// tk_dev_free only after the work using it has completed
+void* tk_dev_alloc(tucker_ctx* c, size_t bytes);
+void tk_dev_free(tucker_ctx* c, void* p, size_t bytes);
 void tk_phase_begin(tucker_ctx* c, int phase, cudaStream_t s);
 void tk_phase_end(tucker_ctx* c, cudaStream_t s);
 void tk_launched(tucker_ctx* c, int phase, int n = 1);
@@ -161,6 +188,10 @@ void tk_radix_sort_pairs(uint32_t* keys, int32_t* vals, uint32_t* keys_alt, int3
                          int bits, void* tmp, cudaStream_t s, uint32_t** keys_out, int32_t** vals_out);
 
 // ---- partition (tk_partition.cu) ----
+// Histograms (with coordinate validation) and popularity labels of every mode;
+// fills c->relabel / c->unlabel / c->fiber.  Throws TUCKER_ERR_INDEX on an
+// out-of-range coordinate.
+void tk_relabel_modes(tucker_ctx* c, const int32_t* const* d_idx, cudaStream_t s);
 void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const void* d_val, int P,
                        cudaStream_t s);
 void tk_partition_export(tucker_ctx* c, int n, int64_t* d_bin_ptr, int32_t* d_perm, cudaStream_t s);
@@ -183,8 +214,10 @@ void tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, si
                 cudaStream_t s);
 
 // ---- factor update (tk_factor.cu) ----
-void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, double* sigma_out,
-                      cudaStream_t s);
+// F_out[row_map[r]] = U[r] (row_map = row_id for a caller's buffer, frow for
+// the context's relabelled factor buffers); other rows zero.
+void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, const int32_t* row_map,
+                      double* sigma_out, cudaStream_t s);
 void tk_alloc_fuws(tucker_ctx* c, int n);
 
 // ---- core / fit (tk_core.cu) ----
@@ -197,8 +230,9 @@ cudaTextureObject_t tk_factor_tex(const tucker_ctx* c, const void* F);
 double tk_norm2(tucker_ctx* c, const void* vals, int64_t n, cudaStream_t s);
 
 // ---- small device utilities ----
+// dst[dst_map ? dst_map[r] : r][0..ldd) = src[src_map ? src_map[r] : r][0..cols), zero padded
 void tk_copy_factor(tucker_ctx* c, const void* src, int lds, void* dst, int ldd, int64_t rows, int cols,
-                    cudaStream_t s);
+                    const int32_t* dst_map, const int32_t* src_map, cudaStream_t s);
 
 #define TK_CUDA(x) tk_check_cuda((x), #x)
 

@@ -25,12 +25,13 @@ __device__ double block_sum_fixed(double v, double* red) {
   return red[32];
 }
 
-// Gpart[split][k][c] = sum over the split's rows r of F[row_id[r]][k] * Z[r][c].
+// Gpart[split][k][c] = sum over the split's rows r of F[frow[r]][k] * Z[r][c] (F is one of the
+// context's factor buffers, whose rows are popularity labels: frow[r] = label of compact row r).
 // Thread owns column c; rows in batches of 32 (factor rows staged in shared
 // memory), batch sums in T added into FP64 accumulators.
 template <typename T, int KM>
 __global__ void __launch_bounds__(128) k_core_partial(const T* __restrict__ Z, int R, int Khat,
-                                                      const int32_t* __restrict__ row_id, const T* __restrict__ F,
+                                                      const int32_t* __restrict__ frow, const T* __restrict__ F,
                                                       int ldF, int K, int rows_per_split, double* __restrict__ Gpart) {
   __shared__ T fr[32][KM];
   const int c = blockIdx.x * 128 + threadIdx.x;
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(128) k_core_partial(const T* __restrict__ Z, i
   for (int rb = r0; rb < r1; rb += 32) {
     for (int i = threadIdx.x; i < 32 * KM; i += 128) {
       const int r = i / KM, k = i - r * KM;
-      fr[r][k] = (rb + r < r1 && k < K) ? F[(int64_t)row_id[rb + r] * ldF + k] : T(0);
+      fr[r][k] = (rb + r < r1 && k < K) ? F[(int64_t)frow[rb + r] * ldF + k] : T(0);
     }
     __syncthreads();
     if (c < Khat) {
@@ -162,9 +163,9 @@ void core_impl(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaS
   dim3 grid(cb, nsplit);
   const T* Z = (const T*)c->Zcore;
   const T* Fn = (const T*)F[n];
-  if (K <= 8) k_core_partial<T, 8><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
-  else if (K <= 16) k_core_partial<T, 16><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
-  else k_core_partial<T, 32><<<grid, 128, 0, s>>>(Z, R, Khat, md.row_id, Fn, ldF[n], K, rps, c->Gpart);
+  if (K <= 8) k_core_partial<T, 8><<<grid, 128, 0, s>>>(Z, R, Khat, md.frow, Fn, ldF[n], K, rps, c->Gpart);
+  else if (K <= 16) k_core_partial<T, 16><<<grid, 128, 0, s>>>(Z, R, Khat, md.frow, Fn, ldF[n], K, rps, c->Gpart);
+  else k_core_partial<T, 32><<<grid, 128, 0, s>>>(Z, R, Khat, md.frow, Fn, ldF[n], K, rps, c->Gpart);
   TK_CUDA(cudaGetLastError());
   FoldInfo fi{};
   fi.N = c->N;
@@ -201,14 +202,13 @@ void tk_core(tucker_ctx* c, void* const* F, const int* ldF, void* G_out, cudaStr
 
 double tk_norm2(tucker_ctx* c, const void* vals, int64_t n, cudaStream_t s) {
   const int nb = (int)std::max<int64_t>(1, std::min<int64_t>(tk_ceil_div(n, 256), 4 * c->sm_count));
-  double* part = nullptr;
-  TK_CUDA(cudaMalloc(&part, (size_t)(nb + 1) * sizeof(double)));
+  double* part = (double*)tk_dev_alloc(c, (size_t)(nb + 1) * sizeof(double));
   if (c->prec == TUCKER_FP32) k_norm2_partial<float><<<nb, 256, 0, s>>>((const float*)vals, n, part, c->err);
   else k_norm2_partial<double><<<nb, 256, 0, s>>>((const double*)vals, n, part, c->err);
   k_sum_final<<<1, 256, 0, s>>>(part, nb, part + nb);
   double out = 0.0;
   TK_CUDA(cudaMemcpyAsync(&out, part + nb, sizeof(double), cudaMemcpyDeviceToHost, s));
   TK_CUDA(cudaStreamSynchronize(s));
-  cudaFree(part);
+  tk_dev_free(c, part, (size_t)(nb + 1) * sizeof(double));
   return out;
 }

@@ -8,7 +8,7 @@
 //   U = Z V Sigma^-1     back-projection
 //   U <- U R^-1 twice    CholeskyQR2 (Gram reductions, Cholesky and inverses in FP64)
 //   signs                column's entry of largest magnitude (lowest slice id on a tie) made positive
-//   F_n[row_id[r]] = U[r], rows of empty slices zero
+//   F_n[row_map[r]] = U[r] (row_map: slice ids, or the context's popularity labels), other rows zero
 #include <algorithm>
 #include <type_traits>
 
@@ -1813,7 +1813,8 @@ void setup_eig_attr() {
 }
 
 template <typename T>
-void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out, double* sigma_out, cudaStream_t s) {
+void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out, const int32_t* row_map,
+                 double* sigma_out, cudaStream_t s) {
   const tk_mode& md = c->mode[n];
   tk_fuws* ws = &c->fu[n];
   const int R = md.R, Khat = md.Khat, K = c->K[n];
@@ -1966,7 +1967,7 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
       k_apply<T, KM><<<nab, 256, 0, s>>>(U, R, K, R2, ws->colbest);
       k_signs<<<1, 32 * K, 0, s>>>(ws->colbest, nab, K, sign);
       TK_CUDA(cudaMemsetAsync(F_out, 0, (size_t)c->L[n] * ldF_out * sizeof(T), s));
-      k_scatter_rows<T, KM><<<gs, 256, 0, s>>>(U, R, K, md.row_id, sign, (T*)F_out, ldF_out);
+      k_scatter_rows<T, KM><<<gs, 256, 0, s>>>(U, R, K, row_map, sign, (T*)F_out, ldF_out);
     };
     if (K <= 8) tail(std::integral_constant<int, 8>());
     else if (K <= 12) tail(std::integral_constant<int, 12>());
@@ -1981,9 +1982,10 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
 
 }  // namespace
 
-void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, double* sigma_out, cudaStream_t s) {
-  if (c->prec == TUCKER_FP32) factor_impl<float>(c, n, Z, F_out, ldF_out, sigma_out, s);
-  else factor_impl<double>(c, n, Z, F_out, ldF_out, sigma_out, s);
+void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_out, const int32_t* row_map,
+                      double* sigma_out, cudaStream_t s) {
+  if (c->prec == TUCKER_FP32) factor_impl<float>(c, n, Z, F_out, ldF_out, row_map, sigma_out, s);
+  else factor_impl<double>(c, n, Z, F_out, ldF_out, row_map, sigma_out, s);
 }
 
 // Per-mode factor-update workspace, sized for that mode.

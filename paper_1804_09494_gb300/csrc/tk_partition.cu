@@ -12,8 +12,11 @@
 //    range [G_p, G_p + g(p)), G = exclusive scan of the gaps g(p) = limit - h(p).
 //    Stream position x therefore belongs to bin max{p : G_p <= x}, which
 //    automatically has g(p) > 0.
-// Tie-breaks: empty slices dropped; sort by (size, slice id); the elements a
-// stage-2 piece takes are the slice's next ones in original COO order.
+// Tie-breaks: empty slices dropped; sort by (size, slice id); inside a slice
+// the elements are listed by the popularity label of their coordinate along
+// the fiber mode f(n) (the other mode with the smallest length), then in
+// original COO order, and a stage-2 piece takes the slice's next ones in that
+// order.  The copy stores every other coordinate as its popularity label.
 #include <algorithm>
 
 #include "tk_common.cuh"
@@ -24,8 +27,7 @@ struct IdxPtrs {
   const int32_t* p[TK_MAXN];
 };
 
-__global__ void k_hist_validate(const int32_t* __restrict__ idx, int64_t nnz, int64_t Ln, int32_t* cnt,
-                                uint32_t* keys, int32_t* vals, int* err) {
+__global__ void k_hist_validate(const int32_t* __restrict__ idx, int64_t nnz, int64_t Ln, int32_t* cnt, int* err) {
   // the whole warp iterates together (stride is a multiple of 32) so the
   // full-mask match below is always executed by all 32 lanes
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -41,11 +43,48 @@ __global__ void k_hist_validate(const int32_t* __restrict__ idx, int64_t nnz, in
     const unsigned peers = __match_any_sync(0xffffffffu, key);
     const int leader = __ffs(peers) - 1;
     if (ok && lane == leader) atomicAdd(&cnt[l], __popc(peers));
-    if (in) {
-      keys[e] = ok ? (uint32_t)l : 0u;
-      vals[e] = (int32_t)e;
-    }
   }
+}
+
+// Popularity sort input: key = nnz - cnt (ascending key = decreasing
+// cardinality), value = slice id (id order, so the stable sort breaks ties
+// by lower id and lists empty slices last).
+__global__ void k_popularity_keys(const int32_t* cnt, int64_t Ln, int64_t nnz, uint32_t* keys, int32_t* vals) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; l < Ln; l += stride) {
+    keys[l] = (uint32_t)(nnz - cnt[l]);
+    vals[l] = (int32_t)l;
+  }
+}
+
+__global__ void k_labels(const int32_t* order, int64_t Ln, int32_t* relabel, int32_t* unlabel) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < Ln; i += stride) {
+    relabel[order[i]] = (int32_t)i;
+    unlabel[i] = order[i];
+  }
+}
+
+// Listing order inside a slice, first key: the popularity label of the
+// element's fiber-mode coordinate (value = element id, so ties keep COO order).
+__global__ void k_fiber_keys(const int32_t* __restrict__ idx_f, const int32_t* __restrict__ relabel_f, int64_t nnz,
+                             uint32_t* keys, int32_t* vals) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += stride) {
+    keys[e] = (uint32_t)relabel_f[idx_f[e]];
+    vals[e] = (int32_t)e;
+  }
+}
+
+// Second (major) key: the slice id of each element in the current order.
+__global__ void k_slice_keys(const int32_t* __restrict__ idx_n, const int32_t* __restrict__ elem, int64_t nnz,
+                             uint32_t* keys) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nnz; i += stride) keys[i] = (uint32_t)idx_n[elem[i]];
+}
+
+__global__ void k_frow(const int32_t* row_id, int R, const int32_t* relabel_n, int32_t* frow) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < R; r += gridDim.x * blockDim.x) frow[r] = relabel_n[row_id[r]];
 }
 
 __global__ void k_nonempty_flags(const int32_t* cnt, int64_t Ln, int32_t* flag) {
@@ -155,6 +194,7 @@ struct ScatterArgs {
   const int64_t* X;
   const int32_t* bhead;
   IdxPtrs idx;
+  IdxPtrs relabel;
   const T* val;
   int N, n, P, t_hat;
   int64_t limit, nnz;
@@ -191,7 +231,7 @@ __global__ void k_scatter(const ScatterArgs<T> a) {
     int q = 0;
     for (int m = 0; m < a.N; ++m) {
       if (m == a.n) continue;
-      a.oidx[q++][dest] = a.idx.p[m][e];
+      a.oidx[q++][dest] = a.relabel.p[m][a.idx.p[m][e]];
     }
     a.oval[dest] = a.val[e];
     a.perm[dest] = e;
@@ -243,20 +283,19 @@ int bitlen(uint64_t x) {
   return b;
 }
 
+// Temporaries of one partition pass, returned when the pass (which ends with a
+// stream synchronisation) goes out of scope.
 struct TmpPool {
-  std::vector<void*> ptrs;
+  tucker_ctx* c;
+  std::vector<std::pair<void*, size_t>> ptrs;
+  explicit TmpPool(tucker_ctx* ctx) : c(ctx) {}
   void* get(size_t bytes) {
-    void* p = nullptr;
-    if (bytes == 0) bytes = 16;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
-      cudaGetLastError();
-      tk_throw(TUCKER_ERR_OOM, "device allocation failed while partitioning");
-    }
-    ptrs.push_back(p);
+    void* p = tk_dev_alloc(c, bytes);
+    ptrs.emplace_back(p, bytes);
     return p;
   }
   ~TmpPool() {
-    for (void* p : ptrs) cudaFree(p);
+    for (auto& q : ptrs) tk_dev_free(c, q.first, q.second);
   }
 };
 
@@ -273,6 +312,42 @@ void launch_scatter(ScatterArgs<T>& a, cudaStream_t s) {
 
 }  // namespace
 
+void tk_relabel_modes(tucker_ctx* c, const int32_t* const* d_idx, cudaStream_t s) {
+  const int64_t nnz = c->nnz;
+  for (int n = 0; n < c->N; ++n) {
+    int f = -1;
+    for (int m = 0; m < c->N; ++m)
+      if (m != n && (f < 0 || c->L[m] < c->L[f])) f = m;
+    c->fiber[n] = f;
+  }
+  for (int m = 0; m < c->N; ++m) {
+    const int64_t Lm = c->L[m];
+    TmpPool tmp(c);
+    int32_t* cnt = (int32_t*)tmp.get(Lm * 4);
+    uint32_t* keys[2] = {(uint32_t*)tmp.get(Lm * 4), (uint32_t*)tmp.get(Lm * 4)};
+    int32_t* vals[2] = {(int32_t*)tmp.get(Lm * 4), (int32_t*)tmp.get(Lm * 4)};
+    void* sort_tmp = tmp.get(tk_sort_tmp_bytes(Lm));
+    TK_CUDA(cudaMemsetAsync(cnt, 0, Lm * 4, s));
+    TK_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), s));
+    k_hist_validate<<<grid_for(nnz), 256, 0, s>>>(d_idx[m], nnz, Lm, cnt, c->err);
+    TK_CUDA(cudaGetLastError());
+    int herr = 0;
+    TK_CUDA(cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    TK_CUDA(cudaStreamSynchronize(s));
+    if (herr & TK_DEV_ERR_INDEX) tk_throw(TUCKER_ERR_INDEX, "a coordinate of mode " + std::to_string(m) + " is outside [0, L)");
+    k_popularity_keys<<<grid_for(Lm), 256, 0, s>>>(cnt, Lm, nnz, keys[0], vals[0]);
+    TK_CUDA(cudaGetLastError());
+    uint32_t* ko;
+    int32_t* vo;
+    tk_radix_sort_pairs(keys[0], vals[0], keys[1], vals[1], Lm, bitlen((uint64_t)nnz), sort_tmp, s, &ko, &vo);
+    c->relabel[m] = (int32_t*)tk_alloc(c, (size_t)Lm * 4);
+    c->unlabel[m] = (int32_t*)tk_alloc(c, (size_t)Lm * 4);
+    k_labels<<<grid_for(Lm), 256, 0, s>>>(vo, Lm, c->relabel[m], c->unlabel[m]);
+    TK_CUDA(cudaGetLastError());
+    TK_CUDA(cudaStreamSynchronize(s));  // temporaries go out of scope
+  }
+}
+
 void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const void* d_val, int P, cudaStream_t s) {
   tk_mode& md = c->mode[n];
   const int64_t nnz = c->nnz;
@@ -284,7 +359,7 @@ void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const 
   md.cap = (int64_t)md.Pa * md.limit;
   if (md.cap >= ((int64_t)1 << 31) - 32) tk_throw(TUCKER_ERR_ARG, "nnz too large for int32 slot indices");
 
-  TmpPool tmp;
+  TmpPool tmp(c);
   int32_t* cnt = (int32_t*)tmp.get(Ln * 4);
   uint32_t* ekey[2] = {(uint32_t*)tmp.get(nnz * 4), (uint32_t*)tmp.get(nnz * 4)};
   int32_t* eval_[2] = {(int32_t*)tmp.get(nnz * 4), (int32_t*)tmp.get(nnz * 4)};
@@ -297,7 +372,7 @@ void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const 
 
   TK_CUDA(cudaMemsetAsync(cnt, 0, Ln * 4, s));
   TK_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), s));
-  k_hist_validate<<<grid_for(nnz), 256, 0, s>>>(d_idx[n], nnz, Ln, cnt, ekey[0], eval_[0], c->err);
+  k_hist_validate<<<grid_for(nnz), 256, 0, s>>>(d_idx[n], nnz, Ln, cnt, c->err);
   TK_CUDA(cudaGetLastError());
   int herr = 0;
   TK_CUDA(cudaMemcpyAsync(&herr, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -319,13 +394,30 @@ void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const 
   int32_t* sval[2] = {(int32_t*)tmp.get((size_t)R * 4), (int32_t*)tmp.get((size_t)R * 4)};
   k_compact_rows<<<grid_for(Ln), 256, 0, s>>>(cnt, Ln, rowidx, md.row_id, skey[0], sval[0]);
   TK_CUDA(cudaGetLastError());
+  md.frow = (int32_t*)tk_alloc(c, (size_t)std::max(R, 1) * 4);
+  k_frow<<<grid_for(R), 256, 0, s>>>(md.row_id, R, c->relabel[n], md.frow);
+  TK_CUDA(cudaGetLastError());
   tk_exclusive_scan_i32(cnt, slice_start, Ln, scan_tmp, s);
 
-  // elements sorted by slice id, original order kept inside a slice
+  // elements in listing order: by slice id, inside a slice by the popularity
+  // label of the fiber-mode coordinate, then by element id (two stable passes,
+  // the minor key first)
+  const int f = c->fiber[n];
+  k_fiber_keys<<<grid_for(nnz), 256, 0, s>>>(d_idx[f], c->relabel[f], nnz, ekey[0], eval_[0]);
+  TK_CUDA(cudaGetLastError());
+  uint32_t* f_key;
+  int32_t* f_val;
+  tk_radix_sort_pairs(ekey[0], eval_[0], ekey[1], eval_[1], nnz, bitlen((uint64_t)(c->L[f] - 1)), scan_tmp, s, &f_key,
+                      &f_val);
+  k_slice_keys<<<grid_for(nnz), 256, 0, s>>>(d_idx[n], f_val, nnz, f_key);
+  TK_CUDA(cudaGetLastError());
   uint32_t* es_key;
   int32_t* es_val;
-  tk_radix_sort_pairs(ekey[0], eval_[0], ekey[1], eval_[1], nnz, bitlen((uint64_t)(Ln - 1)), scan_tmp, s, &es_key,
-                      &es_val);
+  {
+    uint32_t* k_alt = f_key == ekey[0] ? ekey[1] : ekey[0];
+    int32_t* v_alt = f_val == eval_[0] ? eval_[1] : eval_[0];
+    tk_radix_sort_pairs(f_key, f_val, k_alt, v_alt, nnz, bitlen((uint64_t)(Ln - 1)), scan_tmp, s, &es_key, &es_val);
+  }
   // non-empty slices sorted by (cardinality, slice id): the input is in id order and the sort is stable
   uint32_t* ss_key;
   int32_t* ss_val;
@@ -367,10 +459,19 @@ void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const 
   md.gap2 = (int32_t*)tk_alloc(c, (size_t)md.Pa * 4);
   TK_CUDA(cudaMemsetAsync(md.bin_len, 0, (size_t)md.Pa * 4, s));
   TK_CUDA(cudaMemsetAsync(md.gap2, 0, (size_t)md.Pa * 4, s));
+  // every slot of the copy holds valid values: padding slots (past a bin's
+  // length) stay zero -- row 0, coordinate 0, value 0, element 0 -- so the
+  // TTM-chain may read them ahead of use without checks
   md.rowcode = (uint32_t*)tk_alloc(c, (size_t)md.cap * 4);
-  for (int q = 0; q < c->N - 1; ++q) md.oidx[q] = (int32_t*)tk_alloc(c, (size_t)md.cap * 4);
+  TK_CUDA(cudaMemsetAsync(md.rowcode, 0, (size_t)md.cap * 4, s));
+  for (int q = 0; q < c->N - 1; ++q) {
+    md.oidx[q] = (int32_t*)tk_alloc(c, (size_t)md.cap * 4);
+    TK_CUDA(cudaMemsetAsync(md.oidx[q], 0, (size_t)md.cap * 4, s));
+  }
   md.val = tk_alloc(c, (size_t)md.cap * c->esz);
+  TK_CUDA(cudaMemsetAsync(md.val, 0, (size_t)md.cap * c->esz, s));
   md.perm = (int32_t*)tk_alloc(c, (size_t)md.cap * 4);
+  TK_CUDA(cudaMemsetAsync(md.perm, 0, (size_t)md.cap * 4, s));
   TK_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), s));
   k_bins<<<grid_for(P), 256, 0, s>>>(hhat, gap, Gp, P, S2, md.limit, md.bin_len, md.gap2, c->err);
   TK_CUDA(cudaGetLastError());
@@ -385,12 +486,15 @@ void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const 
   }
 
   {
-    IdxPtrs ip{};
-    for (int m = 0; m < c->N; ++m) ip.p[m] = d_idx[m];
+    IdxPtrs ip{}, rl{};
+    for (int m = 0; m < c->N; ++m) {
+      ip.p[m] = d_idx[m];
+      rl.p[m] = c->relabel[m];
+    }
     if (c->prec == TUCKER_FP32) {
       ScatterArgs<float> a{};
       a.skey = es_key; a.sval = es_val; a.slice_start = slice_start; a.t_of = t_of; a.rowidx = rowidx;
-      a.off1 = off1; a.hhat = hhat; a.Gp = Gp; a.X = X; a.bhead = md.split_bhead; a.idx = ip;
+      a.off1 = off1; a.hhat = hhat; a.Gp = Gp; a.X = X; a.bhead = md.split_bhead; a.idx = ip; a.relabel = rl;
       a.val = (const float*)d_val; a.N = c->N; a.n = n; a.P = P; a.t_hat = h_that; a.limit = md.limit; a.nnz = nnz;
       a.rowcode = md.rowcode; for (int q = 0; q < c->N - 1; ++q) a.oidx[q] = md.oidx[q];
       a.oval = (float*)md.val; a.perm = md.perm;
@@ -398,7 +502,7 @@ void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const 
     } else {
       ScatterArgs<double> a{};
       a.skey = es_key; a.sval = es_val; a.slice_start = slice_start; a.t_of = t_of; a.rowidx = rowidx;
-      a.off1 = off1; a.hhat = hhat; a.Gp = Gp; a.X = X; a.bhead = md.split_bhead; a.idx = ip;
+      a.off1 = off1; a.hhat = hhat; a.Gp = Gp; a.X = X; a.bhead = md.split_bhead; a.idx = ip; a.relabel = rl;
       a.val = (const double*)d_val; a.N = c->N; a.n = n; a.P = P; a.t_hat = h_that; a.limit = md.limit; a.nnz = nnz;
       a.rowcode = md.rowcode; for (int q = 0; q < c->N - 1; ++q) a.oidx[q] = md.oidx[q];
       a.oval = (double*)md.val; a.perm = md.perm;
@@ -452,7 +556,8 @@ void tk_partition_mode(tucker_ctx* c, int n, const int32_t* const* d_idx, const 
 
 void tk_partition_export(tucker_ctx* c, int n, int64_t* d_bin_ptr, int32_t* d_perm, cudaStream_t s) {
   tk_mode& md = c->mode[n];
-  TmpPool tmp;
+  c->alloc_stream = s;
+  TmpPool tmp(c);
   void* scan_tmp = tmp.get(tk_scan_tmp_bytes(md.P + 1, 8));
   k_i32_to_i64<<<grid_for(md.P + 1), 256, 0, s>>>(md.bin_len, d_bin_ptr, md.P);
   tk_exclusive_scan_i64(d_bin_ptr, d_bin_ptr, md.P + 1, scan_tmp, s);

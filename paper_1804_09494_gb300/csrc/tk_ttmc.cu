@@ -12,13 +12,16 @@
 // compact Z row once; a split piece goes to a per-bin partial slot and the
 // fix-up adds the pieces in bin order (deterministic, FP64 sums).
 //
-// The kernel is bound by the latency of the two row gathers per element: the
-// F_a row is read through the LSU path and the F_b block through the texture
-// path (two L1 pipelines), the exact FP32 tiles of 3-mode tensors take two
-// elements per step with all four rows requested before either is used (more
-// loads in flight per SM at 8 warps than one element at 12), and the element
-// stream and the Z rows carry an L2 evict-first policy so that the reused
-// factor rows stay in L2.
+// The forward kernel is bound by the two gathered factor rows per element
+// (their L1 misses and the latency behind them), so it keeps as many rows in
+// flight as the registers allow: the rows of the next D elements are requested
+// before the current element is used, and the stream (row code, coordinates,
+// value) is read straight from memory 2D elements ahead, not cached in L1 and
+// marked evict-first in L2.  The F_a row comes through the LSU path, the F_b
+// block through the texture path; factor rows carry an evict-last hint.  The
+// coordinates in the copy are popularity labels and each slice lists its
+// elements by the label of the fiber-mode coordinate, so all threads sweep the
+// hot factor rows together.
 #include <algorithm>
 
 #include "tk_common.cuh"
@@ -66,8 +69,6 @@ struct TtmcArgs {
   T* Zpart;
   // adjoint
   const T* dZ;
-  T* dF[TK_MAXN - 1];
-  int ldd[TK_MAXN - 1];
   T* dval;
 };
 
@@ -160,6 +161,86 @@ __device__ __forceinline__ uint64_t l2_evict_first() {
   asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
+__device__ __forceinline__ uint64_t l2_evict_last() {
+  uint64_t p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// element stream: read once per launch, no L1 allocation, evict-first in L2
+__device__ __forceinline__ uint32_t ld_stream(const uint32_t* p, uint64_t pol) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.b32 %0, [%1], %2;" : "=r"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ int32_t ld_stream(const int32_t* p, uint64_t pol) {
+  return (int32_t)ld_stream((const uint32_t*)p, pol);
+}
+__device__ __forceinline__ float ld_stream(const float* p, uint64_t pol) {
+  float v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double ld_stream(const double* p, uint64_t pol) {
+  double v;
+  asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float2 ld_row2(const float* p, uint64_t pol) {
+  float2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+// gathered factor rows (16-byte vectors), evict-last in L2
+__device__ __forceinline__ float4 ld_row(const float* p, uint64_t pol) {
+  float4 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ double2 ld_row(const double* p, uint64_t pol) {
+  double2 v;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;" : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+}
+__device__ __forceinline__ float4 tex_row_vec(cudaTextureObject_t t, int i, float) { return tex_v4_ordered(t, i); }
+__device__ __forceinline__ double2 tex_row_vec(cudaTextureObject_t t, int i, double) {
+  int4 v;
+  asm volatile("tex.1d.v4.s32.s32 {%0, %1, %2, %3}, [%4, {%5}];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(t), "r"(i));
+  return make_double2(__hiloint2double(v.y, v.x), __hiloint2double(v.w, v.z));
+}
+
+// Store-and-clear of accumulator registers in one asm block: the store is
+// predicated on `on` and the registers are zeroed in place, so that the slice
+// change inside the software-pipelined loop stays a real branch the compiler
+// cannot turn into selects over a second copy of the accumulator.
+__device__ __forceinline__ void st_clear(float* p, float& x, float& y, float& z, float& w, int on, uint64_t pol) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.s32 q, %5, 0;\n"
+      " @q st.global.L2::cache_hint.v4.f32 [%4], {%0, %1, %2, %3}, %6;\n"
+      " mov.b32 %0, 0;\n mov.b32 %1, 0;\n mov.b32 %2, 0;\n mov.b32 %3, 0;\n}"
+      : "+f"(x), "+f"(y), "+f"(z), "+f"(w)
+      : "l"(p), "r"(on), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void st_clear(double* p, double& x, double& y, int on, uint64_t pol) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.s32 q, %3, 0;\n"
+      " @q st.global.L2::cache_hint.v2.f64 [%2], {%0, %1}, %4;\n"
+      " mov.b64 %0, 0;\n mov.b64 %1, 0;\n}"
+      : "+d"(x), "+d"(y)
+      : "l"(p), "r"(on), "l"(pol)
+      : "memory");
+}
+__device__ __forceinline__ void st_clear1(float* p, float& x, int on) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.s32 q, %2, 0;\n @q st.global.f32 [%1], %0;\n mov.b32 %0, 0;\n}"
+               : "+f"(x) : "l"(p), "r"(on) : "memory");
+}
+__device__ __forceinline__ void st_clear1(double* p, double& x, int on) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.s32 q, %2, 0;\n @q st.global.f64 [%1], %0;\n mov.b64 %0, 0;\n}"
+               : "+d"(x) : "l"(p), "r"(on) : "memory");
+}
+
 __device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc),
@@ -209,10 +290,18 @@ __device__ __forceinline__ void issue_chunk(const TtmcArgs<T>& a, char* buf, int
   if (perm) stage_span(vb, a.perm + off, b4, lane);
 }
 
-template <typename T, int MA, int MB, bool EA, bool EB>
-__global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
-  extern __shared__ __align__(16) char smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+constexpr uint32_t kNoCode = 0xFFFFFFFFu;  // no slice yet (row codes stay below 2^31 + 2^30 + 2^30)
+
+// D elements' rows in flight per thread; OUTER: the tensor has outer modes
+// (more than two other modes), whose scalings are gathered with the rows;
+// OVR: values come from a caller's array (by original element id).
+template <typename T, int MA, int MB, bool EA, bool EB, int D, bool OUTER, bool OVR>
+__global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
+  using V = typename VecT<T>::type;
+  constexpr int W = VecT<T>::W;
+  constexpr int NA = Row<T, MA>::NV, NB = Row<T, MB>::NV;
+  constexpr int NQ = OUTER ? TK_MAXN - 3 : 1;
+  const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int g = (int)(gw % a.G);
   const int64_t bw = gw / a.G;
@@ -224,8 +313,8 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
   const int jb = g % a.NB, o = g / a.NB;
   const int j0 = jb * a.TB;
   const int tb = EB ? MB : min(a.TB, a.KB - j0);
-  int oc[TK_MAXN - 3];
-  {
+  int oc[NQ];
+  if (OUTER) {
     int t = o;
     for (int q = 2; q < a.nother; ++q) {
       oc[q - 2] = t % a.Kf[q];
@@ -233,162 +322,154 @@ __global__ void __launch_bounds__(128) k_ttmc_fwd(const TtmcArgs<T> a) {
     }
   }
   const int colbase = a.KA * j0 + a.KA * a.KB * o;
-  const int64_t wbase = bw * a.limit;
-  const int C = a.chunk;
-  const bool sval = a.vals_override == nullptr, sperm = !sval;
-  const int sb = stage_bytes<T>(C, a.nother, sval, sperm);
-  const int CW = C * 32;
-  char* wsm = smem + (size_t)wib * 2 * sb;
+  const int64_t base = bw * a.limit * 32 + lane;  // slot of element k: base + 32 k
+  const uint64_t pf = l2_evict_first(), pl = l2_evict_last();
+  const bool twob = a.nother >= 2;
 
   T acc[MA * MB];
 #pragma unroll
   for (int i = 0; i < MA * MB; ++i) acc[i] = T(0);
+  uint32_t cur = kNoCode;
 
-  auto flush = [&](uint32_t code) {
+  // writes the accumulator to the row (or split slot) of `code` when `on`, and
+  // clears it either way
+  auto flush_clear = [&](uint32_t code, int on) __attribute__((always_inline)) {
     T* dst = (code & TK_SPLIT_BIT) ? a.Zpart + ((int64_t)bin * 2 + ((code & TK_HEAD_BIT) ? 1 : 0)) * a.Khat
                                    : a.Z + (int64_t)(code & TK_ROW_MASK) * a.Khat;
     dst += colbase;
-    if (EA && EB && (MA * MB) % VecT<T>::W == 0 && a.store_vec) {
-      using V = typename VecT<T>::type;
-      V* d = reinterpret_cast<V*>(dst);
+    if (EA && EB && (MA * MB) % W == 0 && a.store_vec) {
 #pragma unroll
-      for (int v = 0; v < MA * MB / VecT<T>::W; ++v) st_stream(d + v, pack(&acc[v * VecT<T>::W]));
+      for (int v = 0; v < MA * MB / W; ++v) {
+        if constexpr (sizeof(T) == 4)
+          st_clear(dst + v * W, acc[v * W], acc[v * W + 1], acc[v * W + 2], acc[v * W + 3], on, pf);
+        else
+          st_clear(dst + v * W, acc[v * W], acc[v * W + 1], on, pf);
+      }
     } else {
 #pragma unroll
       for (int jj = 0; jj < MB; ++jj)
 #pragma unroll
         for (int i = 0; i < MA; ++i)
-          if ((EB || jj < tb) && (EA || i < ka)) dst[i + a.KA * jj] = acc[i + MA * jj];
+          st_clear1(dst + i + a.KA * jj, acc[i + MA * jj], on && (EB || jj < tb) && (EA || i < ka));
     }
   };
 
-  const int nch = (wlen + C - 1) / C;
-  if (nch > 0) issue_chunk(a, wsm, CW, wbase, 0, min(C, wlen), lane, sval, sperm);
-  cp_commit();
-  if (nch > 1) issue_chunk(a, wsm + sb, CW, wbase, C, min(C, wlen - C), lane, sval, sperm);
-  cp_commit();
-  uint32_t cur = len > 0 ? a.rowcode[wbase * 32 + lane] : 0u;
-  // gathers element sj's rows and its outer-mode scaling into v, fa, fb
-  auto gather = [&](const uint32_t* sw, int CW_, int sj, T& v, T (&fa)[Row<T, MA>::R], T (&fb)[Row<T, MB>::R]) {
-    for (int q = 2; q < a.nother; ++q) v *= __ldg(a.F[q] + (int64_t)(int32_t)sw[(1 + q) * CW_ + sj] * a.ld[q] + oc[q - 2]);
-    load_row<T, MA>(a.F[0] + (int64_t)(int32_t)sw[CW_ + sj] * a.ld[0], ka, fa);
-    if (a.nother >= 2) {
-      const int64_t rb = (int64_t)(int32_t)sw[2 * CW_ + sj] * a.ld[1] + j0;
-      if (a.texB) tex_row<T, MB>(a.texB, rb, tb, fb);
-      else load_row<T, MB>(a.F[1] + rb, tb, fb);
-    } else {
-#pragma unroll
-      for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
-    }
+  // coordinates of element k, 2D ahead of use (the row gathers need them
+  // first).  Slot min(k, limit-1) of the bin always holds valid values: an
+  // element, or a padding slot zeroed at init (row 0, value 0, element 0), so
+  // the loads need no select on their results and stay in flight; elements
+  // past the bin's length are never accumulated.
+  int nla[D], nlb[D], nq[D][NQ];
+  auto slot = [&](int k) __attribute__((always_inline)) { return base + (int64_t)min(k, a.limit - 1) * 32; };
+  auto fetch = [&](int d, int k) __attribute__((always_inline)) {
+    const int64_t sl = slot(k);
+    nla[d] = ld_stream(a.oidx[0] + sl, pf);
+    nlb[d] = twob ? ld_stream(a.oidx[1] + sl, pf) : 0;
+    if (OUTER)
+      for (int q = 2; q < a.nother; ++q) nq[d][q - 2] = ld_stream(a.oidx[q] + sl, pf);
   };
-  auto accumulate = [&](uint32_t code, T v, const T (&fa)[Row<T, MA>::R], const T (&fb)[Row<T, MB>::R]) {
-    if (code != cur) {
-      flush(cur);
-#pragma unroll
-      for (int i = 0; i < MA * MB; ++i) acc[i] = T(0);
-      cur = code;
+  // rows of the element whose stream sits in slot d (D ahead of use); an
+  // exact FP32 row whose length is 2 mod 4 ends with an 8-byte load
+  constexpr int RA = (EA && sizeof(T) == 4 && MA % 4 == 2) ? MA : NA * W;
+  constexpr int RB = (EB && sizeof(T) == 4 && MB % 4 == 2) ? MB : NB * W;
+  T A[D][RA], B[D][RB];
+  T v[D], fq[D][NQ];
+  uint32_t code[D];
+  auto issue = [&](int d, int k) __attribute__((always_inline)) {
+    // row code and value of element k, D ahead of use, with its rows
+    {
+      const int64_t sl = slot(k);
+      code[d] = ld_stream(a.rowcode + sl, pf);
+      if (OVR) v[d] = __ldg(a.vals_override + ld_stream(a.perm + sl, pf));
+      else v[d] = ld_stream(a.val + sl, pf);
     }
+    const T* ra = a.F[0] + (int64_t)nla[d] * a.ld[0];
 #pragma unroll
-    for (int jj = 0; jj < MB; ++jj) {
-      const T t = v * fb[jj];
-#pragma unroll
-      for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(fa[i], t, acc[i + MA * jj]);
-    }
-  };
-  for (int c = 0; c < nch; ++c) {
-    cp_wait_1();
-    __syncwarp();
-    const uint32_t* sw = (const uint32_t*)(wsm + (c & 1) * sb);
-    const T* sv = (const T*)(sw + (1 + a.nother) * CW);
-    const int32_t* sp = (const int32_t*)((const char*)sv + (sval ? (size_t)CW * sizeof(T) : 0));
-    // this lane's steps in the chunk
-    const int ns = min(C, len - c * C);
-    if constexpr (sizeof(T) == 4 && EA && EB) {
-      if (a.nother == 2 && a.texB && sval) {
-        // NE elements per step, all their rows requested before the first is used
-        constexpr int NA = Row<T, MA>::NV, NB = Row<T, MB>::NV, NE = TK_TTMC_NE;
-#pragma unroll 1
-        for (int j = 0; j < ns; j += NE) {
-          int sjs[NE];
-          bool has[NE];
-#pragma unroll
-          for (int e = 0; e < NE; ++e) {
-            has[e] = j + e < ns;
-            sjs[e] = (j + (has[e] ? e : 0)) * 32 + lane;
-          }
-          float4 A[NE][NA], B[NE][NB];
-#pragma unroll
-          for (int e = 0; e < NE; ++e) {
-            const T* ra = a.F[0] + (int64_t)(int32_t)sw[CW + sjs[e]] * a.ld[0];
-            const int tb = (int)(((int64_t)(int32_t)sw[2 * CW + sjs[e]] * a.ld[1] + j0) / 4);
-#pragma unroll
-            for (int u = 0; u < NA; ++u) A[e][u] = ldg_v4_ordered(ra + 4 * u);
-#pragma unroll
-            for (int u = 0; u < NB; ++u) B[e][u] = tex_v4_ordered(a.texB, tb + u);
-          }
-          T v[NE];
-          uint32_t code[NE];
-          bool same = true;
-#pragma unroll
-          for (int e = 0; e < NE; ++e) {
-            v[e] = has[e] ? sv[sjs[e]] : T(0);
-            code[e] = sw[sjs[e]];
-            same = same && code[e] == cur;
-          }
-          if (same) {
-#pragma unroll
-            for (int jj = 0; jj < MB; ++jj) {
-              T t[NE];
-#pragma unroll
-              for (int e = 0; e < NE; ++e) t[e] = v[e] * (&B[e][jj / 4].x)[jj % 4];
-#pragma unroll
-              for (int i = 0; i < MA; ++i) {
-                T x = acc[i + MA * jj];
-#pragma unroll
-                for (int e = 0; e < NE; ++e) x = fma((&A[e][i / 4].x)[i % 4], t[e], x);
-                acc[i + MA * jj] = x;
-              }
-            }
-          } else {
-#pragma unroll
-            for (int e = 0; e < NE; ++e) {
-              if (!has[e]) break;
-              T fa[NA * 4], fb[NB * 4];
-#pragma unroll
-              for (int u = 0; u < NA; ++u) unpack(A[e][u], &fa[4 * u]);
-#pragma unroll
-              for (int u = 0; u < NB; ++u) unpack(B[e][u], &fb[4 * u]);
-              accumulate(code[e], v[e], fa, fb);
-            }
-          }
-        }
-        goto chunk_done;
+    for (int u = 0; u < NA; ++u) {
+      if (u * W + W <= RA) {
+        if (EA || u * W < ka) unpack(ld_row(ra + u * W, pl), &A[d][u * W]);
+        else for (int w = 0; w < W; ++w) A[d][u * W + w] = T(0);
+      } else if constexpr (sizeof(T) == 4) {
+        const float2 t = ld_row2((const float*)ra + u * W, pl);
+        A[d][u * W] = t.x;
+        A[d][u * W + 1] = t.y;
       }
     }
-#pragma unroll 1
-    for (int j = 0; j < ns; ++j) {
-      const int sj = j * 32 + lane;
-      T v = sval ? sv[sj] : a.vals_override[sp[sj]];
-      T fa[Row<T, MA>::R], fb[Row<T, MB>::R];
-      gather(sw, CW, sj, v, fa, fb);
-      accumulate(sw[sj], v, fa, fb);
+    if (twob) {
+      const int64_t rb = (int64_t)nlb[d] * a.ld[1] + j0;
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        if (u * W + W <= RB) {
+          if (EB || u * W < tb) unpack(a.texB && RB == NB * W ? tex_row_vec(a.texB, (int)(rb / W) + u, T(0)) : ld_row(a.F[1] + rb + u * W, pl), &B[d][u * W]);
+          else for (int w = 0; w < W; ++w) B[d][u * W + w] = T(0);
+        } else if constexpr (sizeof(T) == 4) {
+          const float2 t = ld_row2((const float*)a.F[1] + rb + u * W, pl);
+          B[d][u * W] = t.x;
+          B[d][u * W + 1] = t.y;
+        }
+      }
     }
-  chunk_done:
-    __syncwarp();
-    if (c + 2 < nch) issue_chunk(a, wsm + (c & 1) * sb, CW, wbase, (c + 2) * C, min(C, wlen - (c + 2) * C), lane, sval, sperm);
-    cp_commit();
+    if (OUTER)
+      for (int q = 2; q < a.nother; ++q) fq[d][q - 2] = __ldg(a.F[q] + (int64_t)nq[d][q - 2] * a.ld[q] + oc[q - 2]);
+  };
+
+#pragma unroll
+  for (int d = 0; d < D; ++d) fetch(d, d);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    issue(d, d);
+    fetch(d, d + D);
   }
-  cp_wait_0();
-  if (len > 0) flush(cur);
+#pragma unroll 1
+  for (int j = 0; j < wlen; j += D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      // element j+d sits in slot d: close the previous slice if it starts a
+      // new one, use the element straight from the slot's registers, then
+      // refill the slot with element j+d+D's rows and element j+d+2D's
+      // coordinates (the other D-1 slots stay in flight meanwhile; no copies,
+      // so the loop carries every slot in the same registers)
+      if (j + d < len) {
+        const uint32_t cd = code[d];
+        if (cd != cur) {
+          flush_clear(cur == kNoCode ? 0u : cur, cur != kNoCode);
+          cur = cd;
+        }
+        T vc = v[d];
+        if (OUTER)
+          for (int q = 2; q < a.nother; ++q) vc *= fq[d][q - 2];
+#pragma unroll
+        for (int jj = 0; jj < MB; ++jj) {
+          const T t = vc * (twob ? B[d][jj] : T(jj == 0));
+#pragma unroll
+          for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(A[d][i], t, acc[i + MA * jj]);
+        }
+      }
+      issue(d, j + d + D);
+      fetch(d, j + d + 2 * D);
+    }
+  }
+  if (len > 0) flush_clear(cur, 1);
 }
 
+// Adjoint, element pass over mode n's copy for one column group g (groups are
+// launched one after another, in order).  A thread walks its bin, stages the
+// cotangent row dZ[row] of each slice once, and for every element computes
+//     dval(e) += so * <fa, D fb>                     (so: outer-mode scalings)
+// and the element's contribution to dF of the target mode m:
+//     m = a:     X[pos_m(e)][i]        (+)= w so sum_j D[i,j] fb[j]
+//     m = b:     X[pos_m(e)][j0 + j]   (+)= w so sum_i D[i,j] fa[i]
+//     m = outer: X[pos_m(e)][oc_m]     (+)= w <fa, D fb> prod_{q != m} F_q[l_q][oc_q]
+// where pos_m(e) is the element's slot in mode m's copy: every slot is
+// written by exactly one thread per launch, so there are no atomics and the
+// order of the sums is fixed.  target < 0: dval only.
 template <typename T, int MA, int MB, bool EA, bool EB>
-__global__ void __launch_bounds__(128) k_ttmc_bwd(const TtmcArgs<T> a) {
+__global__ void __launch_bounds__(128) k_bwd_elem(const TtmcArgs<T> a, int g, int target, int first_dval,
+                                                  int first_x, const int32_t* __restrict__ pos, int Km,
+                                                  T* __restrict__ X) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int g = (int)(gw % a.G);
-  const int64_t bw = gw / a.G;
+  const int64_t bw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (bw * 32 >= a.P) return;
   const int bin = (int)(bw * 32 + lane);
   const int len = a.bin_len[bin];
@@ -449,14 +530,11 @@ __global__ void __launch_bounds__(128) k_ttmc_bwd(const TtmcArgs<T> a) {
         fq[q - 2] = __ldg(a.F[q] + (int64_t)(int32_t)sw[(1 + q) * CW + sj] * a.ld[q] + oc[q - 2]);
         so *= fq[q - 2];
       }
-      const int ia = (int32_t)sw[CW + sj];
       T fa[Row<T, MA>::R];
-      load_row<T, MA>(a.F[0] + (int64_t)ia * a.ld[0], ka, fa);
+      load_row<T, MA>(a.F[0] + (int64_t)(int32_t)sw[CW + sj] * a.ld[0], ka, fa);
       T fb[Row<T, MB>::R];
-      int ib = 0;
       if (a.nother >= 2) {
-        ib = (int32_t)sw[2 * CW + sj];
-        load_row<T, MB>(a.F[1] + (int64_t)ib * a.ld[1] + j0, tb, fb);
+        load_row<T, MB>(a.F[1] + (int64_t)(int32_t)sw[2 * CW + sj] * a.ld[1] + j0, tb, fb);
       } else {
 #pragma unroll
         for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
@@ -478,28 +556,26 @@ __global__ void __launch_bounds__(128) k_ttmc_bwd(const TtmcArgs<T> a) {
 #pragma unroll
       for (int i = 0; i < MA; ++i) dot = fma(fa[i], x[i], dot);
       if (a.dval) {
-        if (a.G == 1) a.dval[e] = so * dot;
-        else atomicAdd(a.dval + e, so * dot);
+        T* dv = a.dval + e;
+        *dv = first_dval ? so * dot : *dv + so * dot;
       }
-      const T ws = w * so;
-      if (a.dF[0]) {
-        T* d = a.dF[0] + (int64_t)ia * a.ldd[0];
+      if (target >= 0) {
+        T* xr = X + (int64_t)pos[e] * Km;
+        const T ws = w * so;
+        if (target == 0) {
 #pragma unroll
-        for (int i = 0; i < MA; ++i)
-          if (EA || i < ka) atomicAdd(d + i, ws * x[i]);
-      }
-      if (a.nother >= 2 && a.dF[1]) {
-        T* d = a.dF[1] + (int64_t)ib * a.ldd[1] + j0;
+          for (int i = 0; i < MA; ++i)
+            if (EA || i < ka) xr[i] = first_x ? ws * x[i] : xr[i] + ws * x[i];
+        } else if (target == 1) {
 #pragma unroll
-        for (int jj = 0; jj < MB; ++jj)
-          if (EB || jj < tb) atomicAdd(d + jj, ws * y[jj]);
-      }
-      for (int q = 2; q < a.nother; ++q) {
-        if (!a.dF[q]) continue;
-        T prod = w * dot;
-        for (int q2 = 2; q2 < a.nother; ++q2)
-          if (q2 != q) prod *= fq[q2 - 2];
-        atomicAdd(a.dF[q] + (int64_t)(int32_t)sw[(1 + q) * CW + sj] * a.ldd[q] + oc[q - 2], prod);
+          for (int jj = 0; jj < MB; ++jj)
+            if (EB || jj < tb) xr[j0 + jj] = first_x ? ws * y[jj] : xr[j0 + jj] + ws * y[jj];
+        } else {
+          T prod = w * dot;
+          for (int q2 = 2; q2 < a.nother; ++q2)
+            if (q2 != target) prod *= fq[q2 - 2];
+          xr[oc[target - 2]] += prod;
+        }
       }
     }
     __syncwarp();
@@ -507,6 +583,73 @@ __global__ void __launch_bounds__(128) k_ttmc_bwd(const TtmcArgs<T> a) {
     cp_commit();
   }
   cp_wait_0();
+}
+
+// Adjoint, reduction over mode m's copy: every slice of mode m sums the
+// contributions X[slot] of its elements in slot order (a thread per Lite bin,
+// registers); whole slices write their compact row of Zc, split pieces the
+// bin's partial slots, which the fix-up adds in bin order.
+template <typename T, int KM>
+__global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int Km, const uint32_t* __restrict__ rowcode,
+                                                    const int32_t* __restrict__ bin_len, int Pa, int limit,
+                                                    T* __restrict__ Zc, T* __restrict__ Zpart) {
+  const int bin = blockIdx.x * blockDim.x + threadIdx.x;
+  if (bin >= Pa) return;
+  const int len = bin_len[bin];
+  const int64_t base = (int64_t)(bin >> 5) * limit * 32 + (bin & 31);
+  T acc[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) acc[k] = T(0);
+  uint32_t cur = 0xFFFFFFFFu;
+  auto flush = [&](uint32_t code) {
+    T* dst = (code & TK_SPLIT_BIT) ? Zpart + ((int64_t)bin * 2 + ((code & TK_HEAD_BIT) ? 1 : 0)) * Km
+                                   : Zc + (int64_t)(code & TK_ROW_MASK) * Km;
+#pragma unroll
+    for (int k = 0; k < KM; ++k)
+      if (k < Km) dst[k] = acc[k];
+  };
+#pragma unroll 1
+  for (int k = 0; k < len; ++k) {
+    const int64_t sl = base + (int64_t)k * 32;
+    const uint32_t code = rowcode[sl];
+    if (code != cur) {
+      if (cur != 0xFFFFFFFFu) flush(cur);
+#pragma unroll
+      for (int q = 0; q < KM; ++q) acc[q] = T(0);
+      cur = code;
+    }
+    const T* xr = X + sl * Km;
+#pragma unroll
+    for (int q = 0; q < KM; ++q)
+      if (q < Km) acc[q] += xr[q];
+  }
+  if (len > 0) flush(cur);
+}
+
+// dF[row_id[r]][k] += Zc[r][k]
+template <typename T>
+__global__ void k_add_rows(const T* __restrict__ Zc, int R, int Km, const int32_t* __restrict__ row_id, T* __restrict__ dF) {
+  const int64_t total = (int64_t)R * Km;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    const int64_t r = i / Km;
+    const int k = (int)(i - r * Km);
+    dF[(int64_t)row_id[r] * Km + k] += Zc[i];
+  }
+}
+
+// pos[perm[slot]] = slot for the occupied slots of a mode's copy
+__global__ void k_inv_pos(const int32_t* __restrict__ perm, const int32_t* __restrict__ bin_len, int Pa, int limit,
+                          int32_t* __restrict__ pos) {
+  const int64_t cap = (int64_t)Pa * limit;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < cap; slot += stride) {
+    const int lane = (int)(slot & 31);
+    const int64_t rest = slot >> 5;
+    const int64_t k = rest % limit;
+    const int p = (int)((rest / limit) * 32 + lane);
+    if (k < bin_len[p]) pos[perm[slot]] = (int32_t)slot;
+  }
 }
 
 // Split-slice fix-up, level 1: one CTA per (chunk of <= 256 bins of one split
@@ -556,14 +699,18 @@ __global__ void k_fixup_final(int Khat, const int32_t* split_chunk0, const int32
   Z[(int64_t)split_row[k] * Khat + col] = (T)s;
 }
 
+// dst[dst_map ? dst_map[r] : r][:] = src[src_map ? src_map[r] : r][:cols], zero padded to ldd
 template <typename T>
-__global__ void k_copy_factor(const T* __restrict__ src, int lds, T* __restrict__ dst, int ldd, int64_t rows, int cols) {
+__global__ void k_copy_factor(const T* __restrict__ src, int lds, T* __restrict__ dst, int ldd, int64_t rows, int cols,
+                              const int32_t* __restrict__ dst_map, const int32_t* __restrict__ src_map) {
   const int64_t total = rows * ldd;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
     const int64_t r = i / ldd;
     const int cc = (int)(i - r * ldd);
-    dst[i] = cc < cols ? src[r * lds + cc] : T(0);
+    const int64_t dr = dst_map ? dst_map[r] : r;
+    const int64_t sr = src_map ? src_map[r] : r;
+    dst[dr * ldd + cc] = cc < cols ? src[sr * lds + cc] : T(0);
   }
 }
 
@@ -580,48 +727,56 @@ constexpr int kNumTiles = 5;
 template <typename T>
 using KernelT = void (*)(TtmcArgs<T>);
 
+// Rows in flight per thread for each tile (register budget: the accumulator
+// plus D elements' rows must stay within 255 registers).
+#define TK_FWD_PICK(T, MA, MB, EA, EB, D)                                                        \
+  (outer ? (ovr ? k_ttmc_fwd<T, MA, MB, EA, EB, D, true, true> : k_ttmc_fwd<T, MA, MB, EA, EB, D, true, false>) \
+         : (ovr ? k_ttmc_fwd<T, MA, MB, EA, EB, D, false, true> : k_ttmc_fwd<T, MA, MB, EA, EB, D, false, false>))
 template <typename T>
-KernelT<T> fwd_kernel(int id);
+KernelT<T> fwd_kernel(int id, bool outer, bool ovr);
 template <>
-KernelT<float> fwd_kernel<float>(int id) {
+KernelT<float> fwd_kernel<float>(int id, bool outer, bool ovr) {
   switch (id) {
-    case 0: return k_ttmc_fwd<float, 10, 10, true, true>;
-    case 1: return k_ttmc_fwd<float, 8, 8, true, true>;
-    case 2: return k_ttmc_fwd<float, 16, 8, true, true>;
-    case 3: return k_ttmc_fwd<float, 16, 8, false, false>;
-    default: return k_ttmc_fwd<float, 32, 4, false, false>;
+    case 0: return TK_FWD_PICK(float, 10, 10, true, true, 4);
+    case 1: return TK_FWD_PICK(float, 8, 8, true, true, 4);
+    case 2: return TK_FWD_PICK(float, 16, 8, true, true, 2);
+    case 3: return TK_FWD_PICK(float, 16, 8, false, false, 2);
+    default: return TK_FWD_PICK(float, 32, 4, false, false, 2);
   }
 }
 template <>
-KernelT<double> fwd_kernel<double>(int id) {
+KernelT<double> fwd_kernel<double>(int id, bool outer, bool ovr) {
   switch (id) {
-    case 0: return k_ttmc_fwd<double, 10, 4, true, false>;
-    case 1: return k_ttmc_fwd<double, 8, 4, true, true>;
-    case 2: return k_ttmc_fwd<double, 16, 4, true, true>;
-    case 3: return k_ttmc_fwd<double, 16, 4, false, false>;
-    default: return k_ttmc_fwd<double, 32, 2, false, false>;
+    case 0: return TK_FWD_PICK(double, 10, 4, true, false, 3);
+    case 1: return TK_FWD_PICK(double, 8, 4, true, true, 3);
+    case 2: return TK_FWD_PICK(double, 16, 4, true, true, 2);
+    case 3: return TK_FWD_PICK(double, 16, 4, false, false, 2);
+    default: return TK_FWD_PICK(double, 32, 2, false, false, 1);
   }
 }
+#undef TK_FWD_PICK
 template <typename T>
-KernelT<T> bwd_kernel(int id);
+using BwdKernelT = void (*)(TtmcArgs<T>, int, int, int, int, const int32_t*, int, T*);
+template <typename T>
+BwdKernelT<T> bwd_kernel(int id);
 template <>
-KernelT<float> bwd_kernel<float>(int id) {
+BwdKernelT<float> bwd_kernel<float>(int id) {
   switch (id) {
-    case 0: return k_ttmc_bwd<float, 10, 10, true, true>;
-    case 1: return k_ttmc_bwd<float, 8, 8, true, true>;
-    case 2: return k_ttmc_bwd<float, 16, 8, true, true>;
-    case 3: return k_ttmc_bwd<float, 16, 8, false, false>;
-    default: return k_ttmc_bwd<float, 32, 4, false, false>;
+    case 0: return k_bwd_elem<float, 10, 10, true, true>;
+    case 1: return k_bwd_elem<float, 8, 8, true, true>;
+    case 2: return k_bwd_elem<float, 16, 8, true, true>;
+    case 3: return k_bwd_elem<float, 16, 8, false, false>;
+    default: return k_bwd_elem<float, 32, 4, false, false>;
   }
 }
 template <>
-KernelT<double> bwd_kernel<double>(int id) {
+BwdKernelT<double> bwd_kernel<double>(int id) {
   switch (id) {
-    case 0: return k_ttmc_bwd<double, 10, 4, true, false>;
-    case 1: return k_ttmc_bwd<double, 8, 4, true, true>;
-    case 2: return k_ttmc_bwd<double, 16, 4, true, true>;
-    case 3: return k_ttmc_bwd<double, 16, 4, false, false>;
-    default: return k_ttmc_bwd<double, 32, 2, false, false>;
+    case 0: return k_bwd_elem<double, 10, 4, true, false>;
+    case 1: return k_bwd_elem<double, 8, 4, true, true>;
+    case 2: return k_bwd_elem<double, 16, 4, true, true>;
+    case 3: return k_bwd_elem<double, 16, 4, false, false>;
+    default: return k_bwd_elem<double, 32, 2, false, false>;
   }
 }
 
@@ -715,11 +870,8 @@ void forward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const vo
   a.store_vec = ((uintptr_t)Z % 16 == 0) && (md.Khat % VecT<T>::W == 0) &&
                 ((pl.KA * pl.tile.MB) % VecT<T>::W == 0);
   a.texB = pl.nother >= 2 ? tk_factor_tex(c, F[pl.others[1]]) : 0;
-  a.chunk = stage_chunk<T>(pl.nother);
-  const int shm = 4 * 2 * stage_bytes<T>(a.chunk, pl.nother, vals_override == nullptr, vals_override != nullptr);
-  set_smem_attr(fwd_kernel<T>(pl.tile_id), shm);
   tk_phase_begin(c, PH_TTM, s);
-  fwd_kernel<T>(pl.tile_id)<<<blocks_for(md, pl.G), 128, shm, s>>>(a);
+  fwd_kernel<T>(pl.tile_id, pl.nother > 2, vals_override != nullptr)<<<blocks_for(md, pl.G), 128, 0, s>>>(a);
   TK_CUDA(cudaGetLastError());
   tk_phase_end(c, s);
   tk_launched(c, PH_TTM);
@@ -737,6 +889,62 @@ void forward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const vo
   }
 }
 
+// Adjoint workspace, allocated by the first backward call of a context:
+// element slots of every mode's copy, the per-slot contributions X, the
+// compact reduction result and the fix-up scratch.
+void ensure_bwd_workspace(tucker_ctx* c, cudaStream_t s) {
+  if (c->bwd_ready) return;
+  c->alloc_stream = s;
+  int64_t xcap = 0, zc = 0, zp = 0, zch = 0;
+  for (int m = 0; m < c->N; ++m) {
+    const tk_mode& md = c->mode[m];
+    xcap = std::max(xcap, md.cap * (int64_t)c->K[m]);
+    zc = std::max(zc, (int64_t)md.R * c->K[m]);
+    zp = std::max(zp, (int64_t)2 * md.Pa * c->K[m]);
+    zch = std::max(zch, (int64_t)md.nchunks * c->K[m]);
+  }
+  for (int m = 0; m < c->N; ++m) {
+    const tk_mode& md = c->mode[m];
+    c->bwd_pos[m] = (int32_t*)tk_alloc(c, (size_t)c->nnz * 4);
+    k_inv_pos<<<(unsigned)std::min<int64_t>(tk_ceil_div(md.cap, 256), 1 << 20), 256, 0, s>>>(md.perm, md.bin_len, md.Pa,
+                                                                                         md.limit, c->bwd_pos[m]);
+    TK_CUDA(cudaGetLastError());
+  }
+  c->bwd_X = tk_alloc(c, (size_t)xcap * c->esz);
+  c->bwd_Zc = tk_alloc(c, (size_t)std::max<int64_t>(zc, 1) * c->esz);
+  c->bwd_Zp = tk_alloc(c, (size_t)std::max<int64_t>(zp, 1) * c->esz);
+  c->bwd_Zch = (double*)tk_alloc(c, (size_t)std::max<int64_t>(zch, 1) * 8);
+  c->bwd_ready = true;
+}
+
+template <typename T>
+void reduce_into(tucker_ctx* c, int m, T* dF, cudaStream_t s) {
+  tk_mode& md = c->mode[m];
+  const int Km = c->K[m];
+  const T* X = (const T*)c->bwd_X;
+  T* Zc = (T*)c->bwd_Zc;
+  T* Zp = (T*)c->bwd_Zp;
+  const unsigned grid = (unsigned)tk_ceil_div(md.Pa, 128);
+  if (Km <= 8) k_bwd_reduce<T, 8><<<grid, 128, 0, s>>>(X, Km, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+  else if (Km <= 16) k_bwd_reduce<T, 16><<<grid, 128, 0, s>>>(X, Km, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+  else k_bwd_reduce<T, 32><<<grid, 128, 0, s>>>(X, Km, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+  TK_CUDA(cudaGetLastError());
+  if (md.nsplit > 0) {
+    dim3 g1(md.nchunks, (unsigned)tk_ceil_div(Km, 32));
+    k_fixup_chunks<T><<<g1, 256, 0, s>>>(Zp, Km, md.chunk_split, md.chunk_b0, md.chunk_b1, md.split_bhead, md.gap2,
+                                         md.split_chunk0, md.split_row, Zc, c->bwd_Zch);
+    TK_CUDA(cudaGetLastError());
+    dim3 g2(md.nsplit, (unsigned)tk_ceil_div(Km, 128));
+    k_fixup_final<T><<<g2, 128, 0, s>>>(Km, md.split_chunk0, md.split_row, c->bwd_Zch, Zc);
+    TK_CUDA(cudaGetLastError());
+  }
+  const int64_t total = (int64_t)md.R * Km;
+  k_add_rows<T><<<(unsigned)std::min<int64_t>(tk_ceil_div(total > 0 ? total : 1, 256), 8192), 256, 0, s>>>(
+      Zc, md.R, Km, md.row_id, dF);
+  TK_CUDA(cudaGetLastError());
+  tk_launched(c, PH_BWD, md.nsplit > 0 ? 4 : 2);
+}
+
 template <typename T>
 void backward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const void* dZ, const void* vals_override,
                    void* const* dF, void* dval, cudaStream_t s) {
@@ -744,20 +952,43 @@ void backward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const v
   const Plan pl = make_plan(c, n);
   TtmcArgs<T> a = make_args<T>(c, n, pl, F, ldF, vals_override);
   a.dZ = (const T*)dZ;
-  for (int q = 0; q < pl.nother; ++q) {
-    a.dF[q] = dF ? (T*)dF[pl.others[q]] : nullptr;
-    a.ldd[q] = c->K[pl.others[q]];
-  }
-  a.dval = (T*)dval;
-  tk_phase_begin(c, PH_BWD, s);
-  if (dval && pl.G > 1) TK_CUDA(cudaMemsetAsync(dval, 0, (size_t)c->nnz * sizeof(T), s));
   a.chunk = stage_chunk<T>(pl.nother);
   const int shm = 4 * 2 * stage_bytes<T>(a.chunk, pl.nother, vals_override == nullptr, true);
-  set_smem_attr(bwd_kernel<T>(pl.tile_id), shm);
-  bwd_kernel<T>(pl.tile_id)<<<blocks_for(md, pl.G), 128, shm, s>>>(a);
-  TK_CUDA(cudaGetLastError());
+  BwdKernelT<T> kern = bwd_kernel<T>(pl.tile_id);
+  set_smem_attr(kern, shm);
+  const unsigned grid = blocks_for(md, 1);
+  tk_phase_begin(c, PH_BWD, s);
+  ensure_bwd_workspace(c, s);
+  // the element passes of the first target also produce dval; without any
+  // target, dval alone
+  bool dval_done = dval == nullptr;
+  for (int q = 0; q < pl.nother; ++q) {
+    const int m = pl.others[q];
+    if (!dF || !dF[m]) continue;
+    const int Km = c->K[m];
+    if (q >= 2) TK_CUDA(cudaMemsetAsync(c->bwd_X, 0, (size_t)c->mode[m].cap * Km * sizeof(T), s));
+    a.dval = dval_done ? nullptr : (T*)dval;
+    for (int g = 0; g < pl.G; ++g) {
+      // X of mode a: every group adds to all K_a columns (first group writes);
+      // of mode b: group g owns the column block of jb = g % NB (first outer
+      // combination writes); of an outer mode: zeroed above, always added
+      const int first_x = q == 0 ? g == 0 : (q == 1 ? g < pl.NB : 0);
+      kern<<<grid, 128, shm, s>>>(a, g, q, g == 0, first_x, c->bwd_pos[m], Km, (T*)c->bwd_X);
+      TK_CUDA(cudaGetLastError());
+    }
+    tk_launched(c, PH_BWD, pl.G);
+    dval_done = true;
+    reduce_into<T>(c, m, (T*)dF[m], s);
+  }
+  if (!dval_done) {
+    a.dval = (T*)dval;
+    for (int g = 0; g < pl.G; ++g) {
+      kern<<<grid, 128, shm, s>>>(a, g, -1, g == 0, 0, nullptr, 0, nullptr);
+      TK_CUDA(cudaGetLastError());
+    }
+    tk_launched(c, PH_BWD, pl.G);
+  }
   tk_phase_end(c, s);
-  tk_launched(c, PH_BWD);
 }
 
 }  // namespace
@@ -767,15 +998,10 @@ int tk_ttmc_groups(const tucker_ctx* c, int n) { return make_plan(c, n).G; }
 int tk_ttmc_threads_per_sm(const tucker_ctx* c, int n) {
   const Plan pl = make_plan(c, n);
   int nb = 0;
-  if (c->prec == TUCKER_FP32) {
-    const int shm = 4 * 2 * stage_bytes<float>(stage_chunk<float>(pl.nother), pl.nother, true, false);
-    set_smem_attr(fwd_kernel<float>(pl.tile_id), shm);
-    TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_kernel<float>(pl.tile_id), 128, shm));
-  } else {
-    const int shm = 4 * 2 * stage_bytes<double>(stage_chunk<double>(pl.nother), pl.nother, true, false);
-    set_smem_attr(fwd_kernel<double>(pl.tile_id), shm);
-    TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_kernel<double>(pl.tile_id), 128, shm));
-  }
+  if (c->prec == TUCKER_FP32)
+    TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_kernel<float>(pl.tile_id, pl.nother > 2, false), 128, 0));
+  else
+    TK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fwd_kernel<double>(pl.tile_id, pl.nother > 2, false), 128, 0));
   return std::max(1, nb) * 128;
 }
 
@@ -792,11 +1018,13 @@ void tk_ttmc_backward(tucker_ctx* c, int n, void* const* F, const int* ldF, cons
 }
 
 void tk_copy_factor(tucker_ctx* c, const void* src, int lds, void* dst, int ldd, int64_t rows, int cols,
-                    cudaStream_t s) {
+                    const int32_t* dst_map, const int32_t* src_map, cudaStream_t s) {
   const int64_t total = rows * ldd;
   const unsigned grid = (unsigned)std::min<int64_t>(tk_ceil_div(total > 0 ? total : 1, 256), 8192);
-  if (c->prec == TUCKER_FP32) k_copy_factor<float><<<grid, 256, 0, s>>>((const float*)src, lds, (float*)dst, ldd, rows, cols);
-  else k_copy_factor<double><<<grid, 256, 0, s>>>((const double*)src, lds, (double*)dst, ldd, rows, cols);
+  if (c->prec == TUCKER_FP32)
+    k_copy_factor<float><<<grid, 256, 0, s>>>((const float*)src, lds, (float*)dst, ldd, rows, cols, dst_map, src_map);
+  else
+    k_copy_factor<double><<<grid, 256, 0, s>>>((const double*)src, lds, (double*)dst, ldd, rows, cols, dst_map, src_map);
   TK_CUDA(cudaGetLastError());
   tk_launched(c, PH_OTHER);
 }

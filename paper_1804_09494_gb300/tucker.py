@@ -30,9 +30,35 @@ _P64 = ctypes.POINTER(ctypes.c_int64)
 _PD = ctypes.POINTER(ctypes.c_double)
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("prec", _I32), ("P_bins", _I32), ("gauss_seidel", _I32), ("timing", _I32),
-                ("wait_cap", _I32), ("reserved", _I32 * 7)]
+                ("wait_cap", _I32), ("reserved0", _I32), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("alloc_user", _VP), ("reserved", _I32 * 4)]
+
+
+def torch_allocator(device):
+    """(alloc, free) callbacks that hand the library memory from torch's
+    caching allocator on `device` (marshalling only: the library decides what
+    to allocate).  alloc returns NULL when torch cannot allocate."""
+    dev = torch.device(device)
+
+    def _alloc(nbytes, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+        except Exception:  # an exception must not cross the C boundary
+            return None
+
+    def _free(ptr, nbytes, stream, user):
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    return ALLOC_FN(_alloc), FREE_FN(_free)
 
 
 SIGNATURES = {
@@ -112,7 +138,7 @@ class Tucker:
     """
 
     def __init__(self, idx, vals, L, K, prec="fp32", P_bins=0, gauss_seidel=False, timing=False,
-                 wait_cap=0):
+                 wait_cap=0, allocator="torch"):
         self.lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("libtucker needs a CUDA device")
@@ -133,6 +159,12 @@ class Tucker:
         opts.gauss_seidel = int(bool(gauss_seidel))
         opts.timing = int(bool(timing))
         opts.wait_cap = int(wait_cap)
+        # device memory from torch's caching allocator (allocator="torch"), or
+        # the library's own cudaMalloc (allocator=None); the callbacks live as
+        # long as the context
+        self._allocator = torch_allocator(idx.device) if allocator == "torch" else None
+        if self._allocator is not None:
+            opts.alloc, opts.free = self._allocator
         Ls = (ctypes.c_int64 * self.N)(*self.L)
         Ks = (ctypes.c_int32 * self.N)(*self.K)
         rows = [idx[m] for m in range(self.N)]

@@ -34,14 +34,14 @@ def full():
 
 
 def sample_slices(cnt, E_max, rng):
-    """Slices to check: the largest below 1.5M elements (split over hundreds of
-    bins, several fix-up chunks), the largest below 100K, two just longer than
-    one bin, the six lightest and twelve random ones.  (The very heaviest
-    slices hold tens of millions of elements, beyond the oracle's reach here.)"""
+    """Slices to check: the heaviest slice (millions of elements, split over
+    thousands of bins and many fix-up chunks), the largest below 1.5M elements,
+    the largest below 100K, two just longer than one bin, the six lightest and
+    twelve random ones."""
     nz = np.flatnonzero(cnt > 0)
     by_size = nz[np.argsort(cnt[nz], kind="stable")]
     c = cnt[by_size]
-    pick = [by_size[:6], rng.choice(nz, size=12, replace=False)]
+    pick = [by_size[:6], by_size[-1:], rng.choice(nz, size=12, replace=False)]
     for cap in (1_500_000, 100_000):
         j = np.searchsorted(c, cap, side="right") - 1
         if j >= 0:
@@ -77,8 +77,9 @@ def test_fullsize_ttm_chain_sampled_rows(full, n):
     Zo = oracle_rows(w, full["Fo"], n, ids)
     assert rel_err(Zg, Zo) <= TTM_TOL["fp32"], (n, rel_err(Zg, Zo))
     assert row_rel_err(Zg, Zo) <= ROW_TOL["fp32"], (n, "row", row_rel_err(Zg, Zo))
-    # the heaviest sampled slice alone (the most split pieces)
+    # the heaviest slice alone (the most split pieces)
     h = int(np.argmax(cnt[ids]))
+    assert cnt[ids[h]] == cnt.max() and cnt[ids[h]] > 100 * tk.stats(n)["E_max"]
     assert rel_err(Zg[h], Zo[h]) <= TTM_TOL["fp32"], (n, int(ids[h]), int(cnt[ids[h]]))
 
 
@@ -98,3 +99,28 @@ def test_fullsize_factor_update(full, n):
     empty = np.ones(Fg.shape[0], dtype=bool)
     empty[rid] = False
     assert not np.any(Fg[empty])
+
+
+def test_hooi_invocation_20M_matches_oracle():
+    """One HOOI invocation (Fig. 1) plus core and fit on the benchmark recipe
+    at 20M nonzeros, in the launch configuration the benchmark times, against
+    the FP64 oracle's: factor subspaces within projector distance 1e-4, fit
+    within 1e-6."""
+    w = synth.workload(WORKLOAD, nnz=20_000_000)
+    L, K = w["L"], w["K"]
+    F0 = synth.random_orthonormal_factors(L, K, seed=1234)
+    Fr = [f.astype(np.float32).astype(np.float64) for f in F0]
+    tk = Tucker(torch.from_numpy(w["idx"]).cuda(), torch.from_numpy(w["vals"]).cuda(), L, K, prec="fp32")
+    try:
+        F = [torch.from_numpy(f).float().cuda() for f in Fr]
+        G, fit = tk.hooi_iter(F)
+        torch.cuda.synchronize()
+        idx = w["idx"].astype(np.int64)
+        v = w["vals"].astype(np.float64)
+        Fo = O.hooi_invocation(L, idx, v, Fr)
+        fo = O.fit(v, O.core(L, idx, v, Fo))
+        for m in range(3):
+            assert O.projector_distance(F[m].double().cpu().numpy(), Fo[m]) <= PROJ_FP32, m
+        assert abs(fit - fo) <= 1e-6, (fit, fo)
+    finally:
+        tk.close()
