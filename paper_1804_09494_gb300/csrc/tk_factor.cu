@@ -1830,6 +1830,13 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
       tk_gram_tc(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->Wpart_elems, ws->W, s);
       tk_launched(c, PH_GRAM, 2);
       gram_done = true;
+    } else if (tk_gram_tiles_supported(Khat) && ((uintptr_t)Z % 16 == 0) &&
+               (size_t)tk_gram_tiles_splits(c, Khat, R) * tk_gram_tiles_pairs(Khat) * 128 * 128 <= ws->Wpart_elems &&
+               tk_gram_tiles_pairs(Khat) <= ws->gram_tiles_cap) {
+      // tensor cores, 128 x 128 blocks of W
+      tk_gram_tiles(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->gram_tiles, ws->W, s);
+      tk_launched(c, PH_GRAM, 2);
+      gram_done = true;
     }
   }
   if (!gram_done) {
@@ -1998,9 +2005,15 @@ void tk_alloc_fuws(tucker_ctx* c, int n) {
   const int tpd = (int)tk_ceil_div(Khat, TM);
   const int ntiles = tpd * (tpd + 1) / 2;
   w.Wpart_elems = (size_t)(2 * sms + ntiles) * TM * TM;
-  w.Wpart = tk_alloc(c, w.Wpart_elems * esz);
   w.gram_tiles_cap = ntiles;
-  w.gram_tiles = (int2*)tk_alloc(c, (size_t)ntiles * sizeof(int2));
+  if (esz == 4 && tk_gram_tiles_supported(Khat)) {
+    // tensor-core blocks: one 128 x 128 tile per (split, block pair)
+    const size_t need = (size_t)tk_gram_tiles_splits(c, Khat, md.R) * tk_gram_tiles_pairs(Khat) * 128 * 128;
+    w.Wpart_elems = std::max(w.Wpart_elems, need);
+    w.gram_tiles_cap = std::max(ntiles, tk_gram_tiles_pairs(Khat));
+  }
+  w.Wpart = tk_alloc(c, w.Wpart_elems * esz);
+  w.gram_tiles = (int2*)tk_alloc(c, (size_t)w.gram_tiles_cap * sizeof(int2));
   w.W = (double*)tk_alloc(c, (size_t)Khat * Khat * 8);
   w.eigA = tk_alloc(c, (size_t)Khat * Khat * esz);
   w.eigV = tk_alloc(c, (size_t)Khat * Khat * esz);

@@ -35,7 +35,11 @@ def aligned_core(G, F, Fo, K):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("L,nnz,zipf,K", [((200, 150, 100), 20_000, None, (8, 8, 8)),
                                          ((3000, 2000, 500), 200_000, (1.1, 1.1, 1.1), (10, 10, 10)),
-                                         ((400, 300, 60, 20), 100_000, (1.2, 1.2, None, None), (6, 5, 4, 3))])
+                                         ((400, 300, 60, 20), 100_000, (1.2, 1.2, None, None), (6, 5, 4, 3)),
+                                         # Khat = 256, 512, 1000: the Gram in 128 x 128 blocks (ragged last block at 1000)
+                                         ((2000, 1500, 300), 60_000, (1.1, 1.1, 1.1), (16, 16, 16)),
+                                         ((500, 500, 80, 30), 80_000, (1.3, 1.3, 1.3, 1.3), (8, 8, 8, 8)),
+                                         ((400, 300, 60, 20), 100_000, (1.2, 1.2, None, None), (10, 10, 10, 10))])
 def test_factor_update_matches_oracle(L, nnz, zipf, K, prec):
     c = case(L, nnz, zipf, "lognormal", seed=31)
     tk = make(c, K, prec)
