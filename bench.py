@@ -44,6 +44,11 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=CPU_SAMPLE)
+    ap.add_argument("--adjoint", action="store_true",
+                    help="a step also runs the adjoint of every mode's TTM-chain (dL/dF_m and dL/dvals for a fixed "
+                         "cotangent dZ_n), the differentiable use of the path")
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3"],
+                    help="FP32 context with the Gram in split TF32 (fp32) or split BF16 (bf16x3)")
     return ap.parse_args()
 
 
@@ -152,32 +157,64 @@ def core_mode(w, R):
     return best
 
 
-def oracle_sample_seconds(w, sample, repeats=1):
-    """Times `repeats` oracle HOOI invocations (+ core + fit) on the first
-    `sample` elements, from the same initial factors, in one fresh
-    single-threaded process; returns the mean seconds per invocation."""
+def host_threads():
+    """Host cores the oracle may use: the process's CPU affinity (else nproc)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def oracle_sample_seconds(w, samples, repeats=1):
+    """Times `repeats` oracle HOOI invocations (+ core + fit) on each of the
+    leading `samples` elements of the stream, from the same initial factors,
+    in one fresh process whose BLAS may use every host core (the oracle's
+    element loops are single-threaded numpy).  Returns the mean seconds per
+    invocation for each sample size."""
+    samples = list(samples)
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "sample.npz")
         F0 = w["F0"]
-        np.savez(path, idx=w["idx"][:, :sample], vals=w["vals"][:sample], L=np.array(w["L"]),
+        top = max(samples)
+        np.savez(path, idx=w["idx"][:, :top], vals=w["vals"][:top], L=np.array(w["L"]),
                  **{f"F{m}": F0[m] for m in range(len(F0))})
         code = (
             "import sys, time, numpy as np; sys.path.insert(0, %r)\n"
             "from oracle import tucker_oracle as O\n"
             "d = np.load(%r); L = tuple(int(x) for x in d['L']); N = len(L)\n"
             "F = [d['F%%d' %% m] for m in range(N)]\n"
-            "idx = d['idx'].astype(np.int64); v = d['vals'].astype(np.float64)\n"
-            "ts = []\n"
-            "for _ in range(%d):\n"
-            "    t = time.perf_counter(); F1 = O.hooi_invocation(L, idx, v, F); G = O.core(L, idx, v, F1)\n"
-            "    f = O.fit(v, G); ts.append(time.perf_counter() - t)\n"
-            "print(sum(ts) / len(ts))\n" % (ROOT, path, int(repeats)))
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+            "idx_all = d['idx'].astype(np.int64); v_all = d['vals'].astype(np.float64)\n"
+            "for n_s in %r:\n"
+            "    idx = idx_all[:, :n_s]; v = v_all[:n_s]; ts = []\n"
+            "    for _ in range(%d):\n"
+            "        t = time.perf_counter(); F1 = O.hooi_invocation(L, idx, v, F); G = O.core(L, idx, v, F1)\n"
+            "        f = O.fit(v, G); ts.append(time.perf_counter() - t)\n"
+            "    print(n_s, sum(ts) / len(ts), flush=True)\n" % (ROOT, path, samples, int(repeats)))
+        nt = str(host_threads())
+        env = dict(os.environ, OMP_NUM_THREADS=nt, OPENBLAS_NUM_THREADS=nt, MKL_NUM_THREADS=nt,
                    CUDA_VISIBLE_DEVICES="")
         r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
         if r.returncode != 0:
             raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-        return float(r.stdout.strip().splitlines()[-1])
+        out = {}
+        for line in r.stdout.strip().splitlines():
+            a, b = line.split()
+            out[int(a)] = float(b)
+        return [out[n_s] for n_s in samples]
+
+
+def extrapolate(samples, secs, nnz):
+    """Least-squares line t = a + b * n through the sampled (n, t), evaluated at
+    nnz; returns (estimate, a, b, largest relative residual)."""
+    x = np.asarray(samples, dtype=np.float64)
+    y = np.asarray(secs, dtype=np.float64)
+    if len(x) < 2:
+        b = float(y[0] / x[0])
+        return b * nnz, 0.0, b, 0.0
+    A = np.stack([np.ones_like(x), x], axis=1)
+    (a, b), *_ = np.linalg.lstsq(A, y, rcond=None)
+    res = float(np.max(np.abs(A @ np.array([a, b]) - y) / y))
+    return float(a + b * nnz), float(a), float(b), res
 
 
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_ttmc_fwd_dram_zipf1.1-2Mx1Mx50K-nnz100M.md")
@@ -240,16 +277,22 @@ def run_reference(args):
     # one process for all steps; the per-step sample shrinks with the step
     # count so that the whole run stays near a minute and a half of oracle time
     sample = min(nnz, args.cpu_sample, max(50_000, args.cpu_sample * 20 // max(args.steps, 1)))
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm state; warm-up steps are not repeated
-    t = float(oracle_sample_seconds(w, sample, repeats=args.steps) * nnz / sample)
+    samples = sorted({max(1, sample // 4), max(1, sample // 2), sample})
+    secs = oracle_sample_seconds(w, samples, repeats=args.steps)
+    t, a, b, res = extrapolate(samples, secs, nnz)
+    threads = host_threads()
     line = dict(metric=METRIC, value=t, unit="s/iter", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=t * 1e3, higher_is_better=False, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", impl="reference",
                 config=dict(workload=args.workload, nnz=nnz, L=list(w["L"]), K=list(w["K"])),
-                cpu_baseline=dict(value=t, unit="s/iter", cores=1, kind="oracle",
-                                  sample=f"first {sample:,} of {nnz:,} elements, {args.steps} HOOI invocations + core "
-                                         f"+ fit in one process (mean), extrapolated linearly in nnz"),
+                cpu_baseline=dict(value=t, unit="s/iter", cores=threads, threads=threads, nproc=os.cpu_count(),
+                                  kind="oracle",
+                                  sample=f"first {', '.join(f'{x:,}' for x in samples)} of {nnz:,} elements, "
+                                         f"{args.steps} HOOI invocations + core + fit each in one process (BLAS on "
+                                         f"{threads} threads; the element loops run on one), s = a + b n fitted "
+                                         f"(a = {a:.3g} s, b = {b:.3g} s/element, largest residual {res:.1%}) and "
+                                         f"evaluated at n = nnz",
+                                  sample_seconds=[round(x, 4) for x in secs]),
                 e2e=dict(value=t, unit="s/iter", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -283,7 +326,7 @@ def run_ours(args):
     # distribution (Lite partition + permuted copies), timed once
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    tk = Tucker(idx_d, vals_d, L, K, prec="fp32", timing=True)
+    tk = Tucker(idx_d, vals_d, L, K, prec=args.prec, timing=True)
     torch.cuda.synchronize()
     partition_s = time.perf_counter() - t0
     R = tk.R
@@ -291,8 +334,22 @@ def run_ours(args):
     F = [torch.from_numpy(f.astype(np.float32)).to(dev) for f in w["F0"]]
     G = torch.empty(int(np.prod(K)), dtype=torch.float32, device=dev)
 
+    # the adjoint's inputs and accumulators live outside the timed region
+    if args.adjoint:
+        gen = torch.Generator(device=dev).manual_seed(17)
+        dZs = [torch.randn(R[n], int(np.prod([K[m] for m in range(N) if m != n])), device=dev, generator=gen)
+               for n in range(N)]
+        dFs = [[None if m == n else torch.zeros(L[m], K[m], device=dev) for m in range(N)] for n in range(N)]
+
+    def step(want_fit):
+        out = tk.hooi_iter(F, G, want_fit=want_fit)
+        if args.adjoint:
+            for n in range(N):
+                tk.ttm_chain_backward(n, F, dZs[n], dF=dFs[n], want_dval=True)
+        return out
+
     for _ in range(args.warmup):
-        tk.hooi_iter(F, G, want_fit=False)
+        step(False)
     tk.timings(reset=True)
     clocks = Clocks(torch.cuda.get_device_properties(dev).uuid and f"GPU-{torch.cuda.get_device_properties(dev).uuid}")
     clocks.start()
@@ -302,7 +359,7 @@ def run_ours(args):
     torch.cuda.nvtx.range_push("timed")  # profilers can restrict a capture to this range
     e0.record(stream)
     for s in range(args.steps):
-        _, fit = tk.hooi_iter(F, G, want_fit=(s == args.steps - 1))
+        _, fit = step(s == args.steps - 1)
     e1.record(stream)
     torch.cuda.nvtx.range_pop()
     barrier()
@@ -344,7 +401,7 @@ def run_ours(args):
     def e2e_step():
         for fd, fh in zip(F, Fh):
             fd.copy_(fh, non_blocking=True)
-        _, fit_e2e = tk.hooi_iter(F, G, want_fit=True)  # the fit is read back to the host
+        _, fit_e2e = step(True)  # the fit is read back to the host
         for fo, fd in zip(Fo, F):
             fo.copy_(fd, non_blocking=True)
         Gh.copy_(G, non_blocking=True)
@@ -389,20 +446,28 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        sample = min(args.cpu_sample, nnz)
-        ts = oracle_sample_seconds(w, sample)
-        cpu = dict(value=ts * nnz / sample, unit="s/iter", cores=1, kind="oracle",
-                   sample=f"first {sample:,} of {nnz:,} elements (same L, K, initial factors); one HOOI invocation "
-                          f"+ core + fit took {ts:.2f} s on one host thread; extrapolated linearly in nnz")
+        top = min(args.cpu_sample, nnz)
+        samples = sorted({max(1, top // 4), max(1, top // 2), top})
+        secs = oracle_sample_seconds(w, samples)
+        est, a, b, res = extrapolate(samples, secs, nnz)
+        threads = host_threads()
+        cpu = dict(value=est, unit="s/iter", cores=threads, threads=threads, nproc=os.cpu_count(), kind="oracle",
+                   sample=f"first {', '.join(f'{x:,}' for x in samples)} of {nnz:,} elements (same L, K, initial "
+                          f"factors): one HOOI invocation + core + fit each, timed in one process with BLAS on "
+                          f"{threads} threads (the element loops run on one); s = a + b n fitted (a = {a:.3g} s, "
+                          f"b = {b:.3g} s/element, largest residual {res:.1%}) and evaluated at n = nnz",
+                   sample_seconds=[round(x, 4) for x in secs])
 
     if rank == 0:
         line = dict(
             metric=METRIC, value=s_per_iter, unit="s/iter", n_gpus=world, steps=args.steps, warmup=args.warmup,
             ms_per_step=t_all / args.steps * 1e3, higher_is_better=False, scaling="weak", vs_baseline=None,
             dtype="f32", data="synthetic",
-            config=dict(workload=args.workload, nnz=nnz, L=list(L), K=list(K), R=R, prec="fp32 TTM-chain, FP32 Gram "
-                        "with FP64 reductions, FP64-polished eigensolve, CholeskyQR2 with FP64 reductions",
+            config=dict(workload=args.workload, nnz=nnz, L=list(L), K=list(K), R=R,
+                        prec="fp32 TTM-chain, Gram on the tensor cores in split " + ("BF16 (three terms)" if args.prec == "bf16x3" else "TF32")
+                        + " with FP64 reductions, FP64-polished eigensolve, CholeskyQR2 with FP64 reductions",
                         l2="inputs larger than L2 (permuted copies ~6 GB per context)",
+                        step="HOOI invocation" + (" + adjoint of every mode's TTM-chain" if args.adjoint else ""),
                         parallelism="replicas" if world > 1 else "single GPU"),
             roofline=dict(bound="hbm", achieved=round(achieved_gbs, 1), peak=pk["hbm_gbs"], unit="GB/s",
                           frac=round(achieved_gbs / pk["hbm_gbs"], 4), traffic=traffic,

@@ -10,9 +10,10 @@
  *    Indices are 0-based (the paper is 1-based).
  *  - Khat_n = prod_{m != n} K[m] is the row length of the penultimate matrix
  *    Z_(n) (Section 2.2); it must be <= 4096.
- *  - Precision: a context is FP32 ("mixed": FP32 TTM-chain, FP32 Gram with
- *    FP64 reductions, FP64 eigen-polish, Cholesky and reductions) or FP64
- *    (plain FP64 everywhere).  Every "real" buffer below is float for FP32
+ *  - Precision: a context is FP32 ("mixed": FP32 TTM-chain, Gram in split
+ *    TF32 -- or split BF16 with TUCKER_BF16X3 -- on the tensor cores with FP64
+ *    reductions, FP64 eigen-polish, Cholesky and reductions) or FP64 (plain
+ *    FP64 everywhere).  Every "real" buffer below is float for FP32 and BF16X3
  *    contexts and double for FP64 contexts, except where double is stated.
  *  - Pointers prefixed d_ are device pointers, h_ are host pointers.  The
  *    caller owns every buffer it passes; the library owns its workspace.
@@ -52,7 +53,18 @@ typedef enum {
   TUCKER_ERR_INDEX = 7     /* an input coordinate lies outside [0, L[m])           */
 } tucker_status;
 
-typedef enum { TUCKER_FP32 = 0, TUCKER_FP64 = 1 } tucker_prec;
+/*
+ * Precision of a context.  TUCKER_FP32 (= TUCKER_TF32X3): FP32 TTM-chain and
+ * values, Gram W = Z^T Z on the tensor cores from z = hi + lo with hi the
+ * TF32-truncated value (W = hi^T hi + hi^T lo + lo^T hi, FP32 accumulation,
+ * FP64 reductions), FP64 eigen-polish and CholeskyQR2.  TUCKER_BF16X3: the same
+ * with every value of Z as three BF16 terms z = b0 + b1 + b2 (round to nearest
+ * each; the rest is O(2^-27 z)) and W from the six products down to order
+ * 2^-18, at the BF16 MMA rate (twice TF32's, so the same time as the three TF32
+ * products; the same accuracy class).  TUCKER_FP64: plain FP64 everywhere
+ * (CUDA cores).
+ */
+typedef enum { TUCKER_FP32 = 0, TUCKER_FP64 = 1, TUCKER_BF16X3 = 2, TUCKER_TF32X3 = TUCKER_FP32 } tucker_prec;
 
 /*
  * Device-memory callbacks.  alloc returns `bytes` bytes of device memory

@@ -216,7 +216,8 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     if (N < 2 || N > TK_MAXN) tk_throw(TUCKER_ERR_ARG, "N must be in [2, 6]");
     if (!L || !K || !d_idx || !d_val) tk_throw(TUCKER_ERR_ARG, "NULL array argument");
     if (nnz < 1 || nnz >= ((int64_t)1 << 31) - 1) tk_throw(TUCKER_ERR_ARG, "nnz must be in [1, 2^31 - 1)");
-    if (o.prec != TUCKER_FP32 && o.prec != TUCKER_FP64) tk_throw(TUCKER_ERR_ARG, "unknown precision");
+    if (o.prec != TUCKER_FP32 && o.prec != TUCKER_FP64 && o.prec != TUCKER_BF16X3)
+      tk_throw(TUCKER_ERR_ARG, "unknown precision");
     if (o.P_bins < 0) tk_throw(TUCKER_ERR_ARG, "P_bins must be >= 0");
     if (o.wait_cap < -1) tk_throw(TUCKER_ERR_ARG, "wait_cap must be >= -1");
     if (o.reserved0) tk_throw(TUCKER_ERR_ARG, "reserved option fields must be zero");
@@ -232,8 +233,9 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     c = new tucker_ctx();
     c->N = N;
     c->nnz = nnz;
-    c->prec = o.prec;
-    c->esz = o.prec == TUCKER_FP32 ? 4 : 8;
+    c->prec = o.prec == TUCKER_FP64 ? TUCKER_FP64 : TUCKER_FP32;
+    c->gram_bf16 = o.prec == TUCKER_BF16X3;
+    c->esz = c->prec == TUCKER_FP32 ? 4 : 8;
     c->gauss_seidel = o.gauss_seidel != 0;
     c->timing = o.timing != 0;
     c->wait_cap = o.wait_cap;

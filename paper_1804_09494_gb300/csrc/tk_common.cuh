@@ -98,7 +98,8 @@ struct tucker_ctx {
   int64_t L[TK_MAXN] = {};
   int32_t K[TK_MAXN] = {};
   int64_t nnz = 0;
-  int prec = TUCKER_FP32;
+  int prec = TUCKER_FP32;   // data precision: TUCKER_FP32 or TUCKER_FP64
+  bool gram_bf16 = false;   // TUCKER_BF16X3: the Gram in split BF16
   size_t esz = 4;
   int gauss_seidel = 0;
   int timing = 0;
@@ -209,11 +210,13 @@ void tk_ttmc_backward(tucker_ctx* c, int n, void* const* F, const int* ldF, cons
 
 // ---- Gram on the tensor cores (tk_gram_tc.cu) ----
 bool tk_gram_tc_supported(int Khat);
-// tiled form for 128 < Khat <= 4096 (Khat % 4 == 0): pairs of 128-column blocks x row splits
+// tiled form for 8 <= Khat <= 4096 (Khat % 4 == 0; used above 128, and at every
+// Khat for the BF16 split): pairs of 128-column blocks x row splits
 bool tk_gram_tiles_supported(int Khat);
 int tk_gram_tiles_pairs(int Khat);
 int tk_gram_tiles_splits(const tucker_ctx* c, int Khat, int R);
-void tk_gram_tiles(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, int2* pairs, double* W, cudaStream_t s);
+void tk_gram_tiles(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, int2* pairs, double* W, bool bf16,
+                   cudaStream_t s);
 // W (FP64, Khat x Khat) = Z^T Z via per-CTA partials in Wpart (>= sm_count 128 x 128 tiles)
 void tk_gram_tc(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, size_t Wpart_elems, double* W,
                 cudaStream_t s);

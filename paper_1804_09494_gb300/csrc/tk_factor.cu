@@ -329,6 +329,162 @@ __device__ void tri_solve(const T* lu, int m, T* x) {
   }
 }
 
+constexpr int kEigSmallThreads = 128;
+
+// Shared phases of the compact eigensolvers (128 threads): the top-K
+// eigenpairs of the m x m tridiagonal (ta, tb) -- Gershgorin interval,
+// multisection, inverse iteration into tri -- and, after the caller's
+// back-transformation into Xs, modified Gram-Schmidt, the FP64 refinement and
+// the scaled output Vs.
+template <typename T>
+struct EigSmem {
+  T* red;
+  double* lo_s;
+  double* hi_s;
+  T* lam_s;
+  T* inv_sig;
+  int* cnt_s;
+  T* mn_s;
+  T* mx_s;
+  T* b2_s;
+};
+
+template <typename T, int NT = kEigSmallThreads>
+__device__ void eig_tridiag_topk(const EigArgs<T>& a, const EigSmem<T>& sh, int m, T* ta, T* tb, T* tb2, T* tri,
+                                 T fro, T eps) {
+  const int K = a.K, tid = threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  constexpr int NW = NT / 32;
+  T* red = sh.red;
+  double* lo_s = sh.lo_s;
+  double* hi_s = sh.hi_s;
+  T* lam_s = sh.lam_s;
+  int* cnt_s = sh.cnt_s;
+  T* mn_s = sh.mn_s;
+  T* mx_s = sh.mx_s;
+  T* b2_s = sh.b2_s;
+  // ---- Gershgorin interval and pivot threshold
+  {
+    T mn = T(INFINITY), mx = T(-INFINITY), b2m = T(0);
+    for (int i = tid; i < m; i += NT) {
+      const T bb = tb[i];
+      tb2[i] = bb * bb;
+      const T r = (i > 0 ? fabs(tb[i - 1]) : T(0)) + fabs(bb);
+      mn = fmin(mn, ta[i] - r);
+      mx = fmax(mx, ta[i] + r);
+      b2m = fmax(b2m, bb * bb);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      b2m = fmax(b2m, __shfl_xor_sync(0xffffffffu, b2m, o));
+    }
+    if (lane == 0) {
+      mn_s[wid] = mn;
+      mx_s[wid] = mx;
+      b2_s[wid] = b2m;
+    }
+    __syncthreads();
+    if (tid < K) {
+      T lo = T(INFINITY), hi = T(-INFINITY);
+      for (int i = 0; i < NW; ++i) {
+        lo = fmin(lo, mn_s[i]);
+        hi = fmax(hi, mx_s[i]);
+      }
+      const T pad = T(1e-6) * (hi - lo) + T(10) * eps * fabs(hi) + T(1e-30);
+      lo_s[tid] = (double)(lo - pad);
+      hi_s[tid] = (double)(hi + pad);
+    }
+    if (tid == 0) {
+      T b2 = T(0);
+      for (int i = 0; i < NW; ++i) b2 = fmax(b2, b2_s[i]);
+      red[0] = (sizeof(T) == 4 ? T(1e-30) : T(1e-290)) * fmax(T(1), b2);
+    }
+    __syncthreads();
+  }
+  const T pivmin = red[0];
+  __syncthreads();
+  // ---- multisection for the K largest eigenvalues of T (NT / K sections each)
+  {
+    const int S = NT / K;
+    const double inv_s1 = 1.0 / (double)(S + 1);
+    // shrink by (S + 1) per round down to FP rounding of the interval width
+    const int rounds = (int)ceil((sizeof(T) == 4 ? 24.0 : 53.0) * 0.6931471805599453 / log((double)(S + 1))) + 1;
+    for (int rd = 0; rd < rounds; ++rd) {
+      const int k = tid / S, sidx = tid - k * S;
+      if (k < K) {
+        const double step = (hi_s[k] - lo_s[k]) * inv_s1;
+        cnt_s[tid] = sturm_count<T>(ta, tb2, m, (T)(lo_s[k] + step * (double)(sidx + 1)), pivmin);
+      }
+      __syncthreads();
+      if (tid < K) {
+        const int target = m - 1 - tid;  // ascending index of the (tid+1)-th largest eigenvalue
+        const double l0 = lo_s[tid], step = (hi_s[tid] - l0) * inv_s1;
+        double nlo = l0, nhi = hi_s[tid];
+        for (int s2 = 0; s2 < S; ++s2) {
+          if (cnt_s[tid * S + s2] <= target) {
+            nlo = l0 + step * (double)(s2 + 1);
+          } else {
+            nhi = l0 + step * (double)(s2 + 1);
+            break;
+          }
+        }
+        lo_s[tid] = nlo;
+        hi_s[tid] = nhi;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid < K) lam_s[tid] = (T)(0.5 * (lo_s[tid] + hi_s[tid]));
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[2] = clock64();
+  // ---- inverse iteration, one thread per eigenvalue, factors in shared memory
+  for (int k = tid; k < K; k += NT) {
+    T* lu = tri + (size_t)k * 6 * m;
+    T* x = lu + 5 * m;
+    const T tiny = eps * fro + T(1e-30);
+    tri_factor<T>(ta, tb, m, lam_s[k], tiny, lu);
+    for (int i = 0; i < m; ++i) x[i] = hash_unit<T>(101 + k, i);
+    for (int it = 0; it < 3; ++it) {
+      tri_solve<T>(lu, m, x);
+      T nn = T(0);
+      for (int i = 0; i < m; ++i) nn = fma(x[i], x[i], nn);
+      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
+      for (int i = 0; i < m; ++i) x[i] *= inv;
+    }
+  }
+  __syncthreads();
+  if (a.clk && tid == 0) a.clk[3] = clock64();
+}
+
+// Early stop of the Lanczos process: after m steps (T_m = tridiag(ta, tb) with
+// tb[m-1] = 0, next coefficient beta) the top-K Ritz pairs of W have residual
+// norms ||W y_k - theta_k y_k|| = beta |s_k[m-1]|, s_k the k-th eigenvector of
+// T_m (into `tri`, K x 6m).  True, for the whole block, when every residual is
+// <= tol * theta_max: the Ritz vectors are then within tol * theta_max / gap
+// of W's eigenvectors, and the FP64 refinement that follows shrinks the rest.
+// Checked from step kLanczosFirstCheck(K) on, every kLanczosCheckEvery steps.
+constexpr int kLanczosCheckEvery = 8;
+__host__ __device__ inline int kLanczosFirstCheck(int K) { return 2 * K + 4; }
+
+template <typename T, int NT>
+__device__ bool lanczos_converged(const EigArgs<T>& a, const EigSmem<T>& sh, int m, T* ta, T* tb, T* tb2, T* tri,
+                                  T beta, T fro, T eps, int* flag) {
+  eig_tridiag_topk<T, NT>(a, sh, m, ta, tb, tb2, tri, fro, eps);
+  if (threadIdx.x == 0) *flag = 1;
+  __syncthreads();
+  const T tol = (sizeof(T) == 4 ? T(2e-6) : T(1e-13)) * fabs(sh.lam_s[0]);
+  if (threadIdx.x < a.K) {
+    const T* x = tri + (size_t)threadIdx.x * 6 * m + 5 * m;
+    if (!(beta * fabs(x[m - 1]) <= tol)) *flag = 0;
+  }
+  __syncthreads();
+  const bool ok = *flag != 0;
+  __syncthreads();
+  return ok;
+}
+
 // Top-K eigenpairs of the symmetric n x n Gram matrix W in one CTA, in the
 // context precision T:
 //   Lanczos tridiagonalisation T = Q^T W Q with full re-orthogonalisation
@@ -349,7 +505,7 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   __shared__ T mn_s[32], mx_s[32], b2_s[32];
   const int n = a.n, K = a.K, tid = threadIdx.x, nt = blockDim.x;
   const int lane = tid & 31, wid = tid >> 5, nw = nt >> 5;
-  const int m = n;
+  int m = n;  // Lanczos steps taken (early stop at convergence)
   unsigned char* p = smem;
   T* A;
   T* Q;
@@ -380,6 +536,8 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   }
   const T fro = sqrt(block_sum<T>(fro2, red));
   const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16);
+  const EigSmem<T> sh_ck{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
+  __shared__ int conv_flag;
   if (a.clk && tid == 0) a.clk[0] = clock64();
 
   // ---- Lanczos
@@ -430,6 +588,15 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
     for (int i = tid; i < n; i += nt) nn = fma(w[i], w[i], nn);
     const T bnorm = sqrt(block_sum<T>(nn, red));
     if (j == m - 1) break;
+    if (j + 1 >= kLanczosFirstCheck(K) && (j + 1 - kLanczosFirstCheck(K)) % kLanczosCheckEvery == 0) {
+      // early stop once the top-K Ritz pairs have converged
+      if (tid == 0) tb[j] = T(0);
+      __syncthreads();
+      if (lanczos_converged<T, 1024>(a, sh_ck, j + 1, ta, tb, tb2, a.tri, bnorm, fro, eps, &conv_flag)) {
+        m = j + 1;
+        break;
+      }
+    }
     T* qn = Q + (size_t)(j + 1) * n;
     if (bnorm > T(100) * eps * fro) {
       if (tid == 0) tb[j] = bnorm;
@@ -454,95 +621,7 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   __syncthreads();
   if (a.clk && tid == 0) a.clk[1] = clock64();
 
-  // ---- Gershgorin interval and pivot threshold
-  {
-    T mn = T(INFINITY), mx = T(-INFINITY), b2m = T(0);
-    for (int i = tid; i < m; i += nt) {
-      const T bb = tb[i];
-      tb2[i] = bb * bb;
-      const T r = (i > 0 ? fabs(tb[i - 1]) : T(0)) + fabs(bb);
-      mn = fmin(mn, ta[i] - r);
-      mx = fmax(mx, ta[i] + r);
-      b2m = fmax(b2m, bb * bb);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      b2m = fmax(b2m, __shfl_xor_sync(0xffffffffu, b2m, o));
-    }
-    if (lane == 0) {
-      mn_s[wid] = mn;
-      mx_s[wid] = mx;
-      b2_s[wid] = b2m;
-    }
-    __syncthreads();
-    if (tid < K) {
-      T lo = T(INFINITY), hi = T(-INFINITY);
-      for (int i = 0; i < nw; ++i) {
-        lo = fmin(lo, mn_s[i]);
-        hi = fmax(hi, mx_s[i]);
-      }
-      const T pad = T(1e-6) * (hi - lo) + T(10) * eps * fabs(hi) + T(1e-30);
-      lo_s[tid] = (double)(lo - pad);
-      hi_s[tid] = (double)(hi + pad);
-    }
-    if (tid == 0) {
-      T b2 = T(0);
-      for (int i = 0; i < nw; ++i) b2 = fmax(b2, b2_s[i]);
-      red[0] = (sizeof(T) == 4 ? T(1e-30) : T(1e-290)) * fmax(T(1), b2);
-    }
-    __syncthreads();
-  }
-  const T pivmin = red[0];
-  __syncthreads();
-  // ---- multisection for the K largest eigenvalues of T
-  const int S = nt / K;
-  const double inv_s1 = 1.0 / (double)(S + 1);
-  const int rounds = sizeof(T) == 4 ? 5 : 9;
-  for (int rd = 0; rd < rounds; ++rd) {
-    const int k = tid / S, sidx = tid - k * S;
-    if (k < K) {
-      const double step = (hi_s[k] - lo_s[k]) * inv_s1;
-      cnt_s[tid] = sturm_count<T>(ta, tb2, m, (T)(lo_s[k] + step * (double)(sidx + 1)), pivmin);
-    }
-    __syncthreads();
-    if (tid < K) {
-      const int target = m - 1 - tid;  // ascending index of the (tid+1)-th largest eigenvalue
-      const double l0 = lo_s[tid], step = (hi_s[tid] - l0) * inv_s1;
-      double nlo = l0, nhi = hi_s[tid];
-      for (int s2 = 0; s2 < S; ++s2) {
-        if (cnt_s[tid * S + s2] <= target) {
-          nlo = l0 + step * (double)(s2 + 1);
-        } else {
-          nhi = l0 + step * (double)(s2 + 1);
-          break;
-        }
-      }
-      lo_s[tid] = nlo;
-      hi_s[tid] = nhi;
-    }
-    __syncthreads();
-  }
-  if (tid < K) lam_s[tid] = (T)(0.5 * (lo_s[tid] + hi_s[tid]));
-  __syncthreads();
-  if (a.clk && tid == 0) a.clk[2] = clock64();
-  // ---- inverse iteration, one thread per eigenvalue
-  for (int k = tid; k < K; k += nt) {
-    T* lu = a.tri + (size_t)k * 6 * m;
-    T* x = lu + 5 * m;
-    const T tiny = eps * fro + T(1e-30);
-    tri_factor<T>(ta, tb, m, lam_s[k], tiny, lu);
-    for (int i = 0; i < m; ++i) x[i] = hash_unit<T>(101 + k, i);
-    for (int it = 0; it < 3; ++it) {
-      tri_solve<T>(lu, m, x);
-      T nn = T(0);
-      for (int i = 0; i < m; ++i) nn = fma(x[i], x[i], nn);
-      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
-      for (int i = 0; i < m; ++i) x[i] *= inv;
-    }
-  }
-  __syncthreads();
+  eig_tridiag_topk<T, 1024>(a, sh_ck, m, ta, tb, tb2, a.tri, fro, eps);
   if (a.clk && tid == 0) a.clk[3] = clock64();
   // ---- X = Q S, then modified Gram-Schmidt (separates clustered eigenvalues)
   for (int idx = tid; idx < n * K; idx += nt) {
@@ -649,7 +728,6 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
 // both the per-k and the per-r sweeps.  The tridiagonal phases and the modified
 // Gram-Schmidt of the eigenvectors work in shared memory; the FP64 refinement
 // is the same as in k_eig.
-constexpr int kEigSmallThreads = 128;
 
 template <typename T>
 __host__ __device__ inline int eig_small_ldq(int n) {
@@ -664,133 +742,6 @@ __host__ __device__ inline size_t eig_small_smem(int n, int K) {
   size_t e = (size_t)n * n + (size_t)n * eig_small_ldq<T>(n) + (size_t)n * K + (size_t)6 * n;
   if (tri > (size_t)n * n) e += tri;
   return (size_t)2 * K * (K + 1) * sizeof(double) + e * sizeof(T);
-}
-
-// Shared phases of the compact eigensolvers (128 threads): the top-K
-// eigenpairs of the m x m tridiagonal (ta, tb) -- Gershgorin interval,
-// multisection, inverse iteration into tri -- and, after the caller's
-// back-transformation into Xs, modified Gram-Schmidt, the FP64 refinement and
-// the scaled output Vs.
-template <typename T>
-struct EigSmem {
-  T* red;
-  double* lo_s;
-  double* hi_s;
-  T* lam_s;
-  T* inv_sig;
-  int* cnt_s;
-  T* mn_s;
-  T* mx_s;
-  T* b2_s;
-};
-
-template <typename T>
-__device__ void eig_tridiag_topk(const EigArgs<T>& a, const EigSmem<T>& sh, int m, T* ta, T* tb, T* tb2, T* tri,
-                                 T fro, T eps) {
-  const int K = a.K, tid = threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
-  constexpr int NT = kEigSmallThreads, NW = NT / 32;
-  T* red = sh.red;
-  double* lo_s = sh.lo_s;
-  double* hi_s = sh.hi_s;
-  T* lam_s = sh.lam_s;
-  int* cnt_s = sh.cnt_s;
-  T* mn_s = sh.mn_s;
-  T* mx_s = sh.mx_s;
-  T* b2_s = sh.b2_s;
-  // ---- Gershgorin interval and pivot threshold
-  {
-    T mn = T(INFINITY), mx = T(-INFINITY), b2m = T(0);
-    for (int i = tid; i < m; i += NT) {
-      const T bb = tb[i];
-      tb2[i] = bb * bb;
-      const T r = (i > 0 ? fabs(tb[i - 1]) : T(0)) + fabs(bb);
-      mn = fmin(mn, ta[i] - r);
-      mx = fmax(mx, ta[i] + r);
-      b2m = fmax(b2m, bb * bb);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      b2m = fmax(b2m, __shfl_xor_sync(0xffffffffu, b2m, o));
-    }
-    if (lane == 0) {
-      mn_s[wid] = mn;
-      mx_s[wid] = mx;
-      b2_s[wid] = b2m;
-    }
-    __syncthreads();
-    if (tid < K) {
-      T lo = T(INFINITY), hi = T(-INFINITY);
-      for (int i = 0; i < NW; ++i) {
-        lo = fmin(lo, mn_s[i]);
-        hi = fmax(hi, mx_s[i]);
-      }
-      const T pad = T(1e-6) * (hi - lo) + T(10) * eps * fabs(hi) + T(1e-30);
-      lo_s[tid] = (double)(lo - pad);
-      hi_s[tid] = (double)(hi + pad);
-    }
-    if (tid == 0) {
-      T b2 = T(0);
-      for (int i = 0; i < NW; ++i) b2 = fmax(b2, b2_s[i]);
-      red[0] = (sizeof(T) == 4 ? T(1e-30) : T(1e-290)) * fmax(T(1), b2);
-    }
-    __syncthreads();
-  }
-  const T pivmin = red[0];
-  __syncthreads();
-  // ---- multisection for the K largest eigenvalues of T (NT / K sections each)
-  {
-    const int S = NT / K;
-    const double inv_s1 = 1.0 / (double)(S + 1);
-    // shrink by (S + 1) per round down to FP rounding of the interval width
-    const int rounds = (int)ceil((sizeof(T) == 4 ? 24.0 : 53.0) * 0.6931471805599453 / log((double)(S + 1))) + 1;
-    for (int rd = 0; rd < rounds; ++rd) {
-      const int k = tid / S, sidx = tid - k * S;
-      if (k < K) {
-        const double step = (hi_s[k] - lo_s[k]) * inv_s1;
-        cnt_s[tid] = sturm_count<T>(ta, tb2, m, (T)(lo_s[k] + step * (double)(sidx + 1)), pivmin);
-      }
-      __syncthreads();
-      if (tid < K) {
-        const int target = m - 1 - tid;  // ascending index of the (tid+1)-th largest eigenvalue
-        const double l0 = lo_s[tid], step = (hi_s[tid] - l0) * inv_s1;
-        double nlo = l0, nhi = hi_s[tid];
-        for (int s2 = 0; s2 < S; ++s2) {
-          if (cnt_s[tid * S + s2] <= target) {
-            nlo = l0 + step * (double)(s2 + 1);
-          } else {
-            nhi = l0 + step * (double)(s2 + 1);
-            break;
-          }
-        }
-        lo_s[tid] = nlo;
-        hi_s[tid] = nhi;
-      }
-      __syncthreads();
-    }
-  }
-  if (tid < K) lam_s[tid] = (T)(0.5 * (lo_s[tid] + hi_s[tid]));
-  __syncthreads();
-  if (a.clk && tid == 0) a.clk[2] = clock64();
-  // ---- inverse iteration, one thread per eigenvalue, factors in shared memory
-  for (int k = tid; k < K; k += NT) {
-    T* lu = tri + (size_t)k * 6 * m;
-    T* x = lu + 5 * m;
-    const T tiny = eps * fro + T(1e-30);
-    tri_factor<T>(ta, tb, m, lam_s[k], tiny, lu);
-    for (int i = 0; i < m; ++i) x[i] = hash_unit<T>(101 + k, i);
-    for (int it = 0; it < 3; ++it) {
-      tri_solve<T>(lu, m, x);
-      T nn = T(0);
-      for (int i = 0; i < m; ++i) nn = fma(x[i], x[i], nn);
-      const T inv = nn > T(0) ? T(1) / sqrt(nn) : T(0);
-      for (int i = 0; i < m; ++i) x[i] *= inv;
-    }
-  }
-  __syncthreads();
-  if (a.clk && tid == 0) a.clk[3] = clock64();
 }
 
 template <typename T>
@@ -898,7 +849,8 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
   __shared__ T mn_s[4], mx_s[4], b2_s[4];
   const int n = a.n, K = a.K, tid = threadIdx.x;
   constexpr int NT = kEigSmallThreads;
-  const int m = n, ldq = eig_small_ldq<T>(n);
+  int m = n;  // Lanczos steps taken (early stop at convergence)
+  const int ldq = eig_small_ldq<T>(n);
   // Cholesky factor C and its inverse Ri (refinement), K x (K + 1) row-major
   double* Cm = (double*)smem;
   double* Rm = Cm + K * (K + 1);
@@ -920,6 +872,8 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
   }
   const T fro = sqrt(block_sum<T>(fro2, red));
   const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16);
+  const EigSmem<T> sh_ck{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
+  __shared__ int conv_flag;
   if (a.clk && tid == 0) a.clk[0] = clock64();
 
   // rows owned by this thread (n <= 2 * NT)
@@ -1006,6 +960,15 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
     if (tid == 0) ta[j] = al;
     const T bnorm = sqrt(block_sum<T>(w0 * w0 + w1 * w1, red));
     if (j == m - 1) break;
+    if (j + 1 >= kLanczosFirstCheck(K) && (j + 1 - kLanczosFirstCheck(K)) % kLanczosCheckEvery == 0) {
+      // early stop once the top-K Ritz pairs have converged
+      if (tid == 0) tb[j] = T(0);
+      __syncthreads();
+      if (lanczos_converged<T, 128>(a, sh_ck, j + 1, ta, tb, tb2, a.tri, bnorm, fro, eps, &conv_flag)) {
+        m = j + 1;
+        break;
+      }
+    }
     if (bnorm > T(100) * eps * fro) {
       if (tid == 0) tb[j] = bnorm;
       const T inv = T(1) / bnorm;
@@ -1083,7 +1046,8 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_v4(const EigArgs<float
   __shared__ float mn_s[4], mx_s[4], b2_s[4];
   const int n = a.n, K = a.K, tid = threadIdx.x;
   constexpr int NT = kEigSmallThreads;
-  const int m = n, ld = eig_v4_ld(n), np = (n + 3) & ~3, np4 = np / 4;
+  int m = n;  // Lanczos steps taken (early stop at convergence)
+  const int ld = eig_v4_ld(n), np = (n + 3) & ~3, np4 = np / 4;
   double* Cm = (double*)smem;
   double* Rm = Cm + K * (K + 1);
   float* A = (float*)(Rm + K * (K + 1));  // n x ld, row r = W[r][:]
@@ -1109,6 +1073,8 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_v4(const EigArgs<float
   for (int i = tid; i < 2 * np; i += NT) ws[i] = 0.f;  // ws and hs, including padding
   const float fro = sqrtf(block_sum<float>(fro2, red));
   const float eps = 1.2e-7f;
+  const EigSmem<float> sh_ck{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
+  __shared__ int conv_flag;
   if (a.clk && tid == 0) a.clk[0] = clock64();
 
   const int r = tid;
@@ -1174,6 +1140,15 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_v4(const EigArgs<float
     if (tid == 0) ta[j] = al;
     const float bnorm = sqrtf(block_sum<float>(w * w, red));
     if (j == m - 1) break;
+    if (j + 1 >= kLanczosFirstCheck(K) && (j + 1 - kLanczosFirstCheck(K)) % kLanczosCheckEvery == 0) {
+      // early stop once the top-K Ritz pairs have converged
+      if (tid == 0) tb[j] = float(0);
+      __syncthreads();
+      if (lanczos_converged<float, 128>(a, sh_ck, j + 1, ta, tb, tb2, a.tri, bnorm, fro, eps, &conv_flag)) {
+        m = j + 1;
+        break;
+      }
+    }
     if (bnorm > 100.f * eps * fro) {
       if (tid == 0) tb[j] = bnorm;
       const float inv = 1.f / bnorm;
@@ -1825,16 +1800,16 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
   tk_phase_begin(c, PH_GRAM, s);
   bool gram_done = false;
   if constexpr (sizeof(T) == 4) {
-    if (tk_gram_tc_supported(Khat) && ((uintptr_t)Z % 16 == 0)) {
+    if (!c->gram_bf16 && tk_gram_tc_supported(Khat) && ((uintptr_t)Z % 16 == 0)) {
       // tensor cores: per-CTA partials, reduced and symmetrised in FP64
       tk_gram_tc(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->Wpart_elems, ws->W, s);
       tk_launched(c, PH_GRAM, 2);
       gram_done = true;
-    } else if (tk_gram_tiles_supported(Khat) && ((uintptr_t)Z % 16 == 0) &&
+    } else if ((Khat > 128 || c->gram_bf16) && tk_gram_tiles_supported(Khat) && ((uintptr_t)Z % 16 == 0) &&
                (size_t)tk_gram_tiles_splits(c, Khat, R) * tk_gram_tiles_pairs(Khat) * 128 * 128 <= ws->Wpart_elems &&
                tk_gram_tiles_pairs(Khat) <= ws->gram_tiles_cap) {
       // tensor cores, 128 x 128 blocks of W
-      tk_gram_tiles(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->gram_tiles, ws->W, s);
+      tk_gram_tiles(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->gram_tiles, ws->W, c->gram_bf16, s);
       tk_launched(c, PH_GRAM, 2);
       gram_done = true;
     }
@@ -2006,7 +1981,7 @@ void tk_alloc_fuws(tucker_ctx* c, int n) {
   const int ntiles = tpd * (tpd + 1) / 2;
   w.Wpart_elems = (size_t)(2 * sms + ntiles) * TM * TM;
   w.gram_tiles_cap = ntiles;
-  if (esz == 4 && tk_gram_tiles_supported(Khat)) {
+  if (esz == 4 && tk_gram_tiles_supported(Khat) && (Khat > 128 || c->gram_bf16)) {
     // tensor-core blocks: one 128 x 128 tile per (split, block pair)
     const size_t need = (size_t)tk_gram_tiles_splits(c, Khat, md.R) * tk_gram_tiles_pairs(Khat) * 128 * 128;
     w.Wpart_elems = std::max(w.Wpart_elems, need);

@@ -28,6 +28,7 @@
 // the CTA waits (bounded) for its copies and MMAs in flight, releases its
 // tensor memory and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
@@ -119,6 +120,35 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
+}
+
+// byte offset of element (m, k) of a K-major 16-bit tile with 64-byte swizzle
+// (rows of 32 elements, 8-row atoms of 512 B; 16-byte chunk index k / 8
+// XORed with address bits 7-8, i.e. (m & 7) >> 1)
+__device__ __forceinline__ uint32_t sw64_off(int m, int k) {
+  const int r8 = m & 7;
+  return (m >> 3) * 512 + r8 * 64 + ((((k >> 3) ^ (r8 >> 1)) & 3) << 4) + (k & 7) * 2;
+}
+
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset between 8-row atoms
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)4 << 61;            // 64-byte swizzle
+  return d;
+}
+
+// kind::f16 instruction descriptor: D FP32, A and B BF16 K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
 struct GramTcArgs {
@@ -377,7 +407,16 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       : "memory");
 }
 
+// BF: every value as three BF16 terms z = b0 + b1 + b2 (round to nearest each,
+// z - b0 - b1 - b2 = O(2^-27 z)) and W from the six products of order up to
+// 2^-18, b0b0 + b0b1 + b1b0 + b0b2 + b2b0 + b1b1, as kind::f16 MMAs (K = 16 per
+// instruction, twice the TF32 rate) on 64-byte swizzled tiles; diagonal blocks
+// take the same six products.  Otherwise split TF32 as described above.
+template <bool BF>
 __global__ void __launch_bounds__(kThreads, 1) k_gram_tiles(const __grid_constant__ CUtensorMap tz, const GramTileArgs a) {
+  constexpr int kOp = BF ? 128 * kBatch * 2 : kOpBytes;  // one operand tile (8 or 16 KB)
+  constexpr int kRowsPer = BF ? 8 : 4;                  // consecutive K (rows) per 16-byte chunk
+  constexpr int NT = BF ? 3 : 2;                        // operand tiles per box
   extern __shared__ __align__(1024) unsigned char smraw[];
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -385,9 +424,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tiles(const __grid_constan
   const int I = a.pairs[pair].x, J = a.pairs[pair].y;
   const bool diag = I == J;
   const int nstrips = diag ? 1 : 2;
-  // layout: operands [2 stages][hi_I, lo_I, hi_J, lo_J] | raw [kTileRaw][2 boxes] | barriers | TMEM slot
+  // layout: operands [2 stages][NT tiles of box I, NT of box J] | raw [kTileRaw][2 boxes] | barriers | TMEM slot
   unsigned char* ops = sm;
-  unsigned char* raw = sm + 8 * kOpBytes;
+  unsigned char* raw = sm + 2 * 2 * NT * kOp;
   uint64_t* raw_full = (uint64_t*)(raw + kTileRaw * 2 * kBoxBytes);
   uint64_t* op_free = raw_full + kTileRaw;
   uint64_t* acc_done = op_free + 2;
@@ -398,7 +437,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tiles(const __grid_constan
   const int64_t r1 = min((int64_t)a.R, r0 + a.rows_per_split);
   const int nrows = (int)max((int64_t)0, r1 - r0);
   const int nb = (nrows + kBatch - 1) / kBatch;
-  const uint32_t idesc = idesc_tf32(128);
+  const uint32_t idesc = BF ? idesc_bf16(128) : idesc_tf32(128);
 
   if (tid == 0) {
     s_fail = 0;
@@ -462,20 +501,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tiles(const __grid_constan
     return true;
   };
 
-  // this thread's (box, column m, 4-row chunk) triples of the transposition
+  // this thread's (box, column m, chunk of kRowsPer rows) triples of the transposition
   constexpr int kXT = kThreads - 32;
-  constexpr int kTP = (2 * 128 * (kBatch / 4) + kXT - 1) / kXT;
+  constexpr int kChunks = kBatch / kRowsPer;
+  constexpr int kTP = (2 * 128 * kChunks + kXT - 1) / kXT;
   int pbox[kTP], pm[kTP], pc[kTP];
   uint32_t poff[kTP];
 #pragma unroll
   for (int i = 0; i < kTP; ++i) {
     const int pidx = (tid - 32) + i * kXT;
-    const int bx = pidx / (128 * (kBatch / 4)), rem = pidx % (128 * (kBatch / 4));
+    const int bx = pidx / (128 * kChunks), rem = pidx % (128 * kChunks);
     const bool live = warp > 0 && bx < nstrips;
     pbox[i] = bx;
     pm[i] = live ? rem % 128 : -1;
     pc[i] = live ? rem / 128 : 0;
-    poff[i] = live ? sw128_off(pm[i], 4 * pc[i]) : 0u;
+    poff[i] = live ? (BF ? sw64_off(pm[i], kRowsPer * pc[i]) : sw128_off(pm[i], kRowsPer * pc[i])) : 0u;
   }
 
   int b = 0;
@@ -491,28 +531,53 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tiles(const __grid_constan
     } else if (warp > 0) {
       const int rows = min(kBatch, nrows - b * kBatch);
       const float* rw = (const float*)(raw + slot * 2 * kBoxBytes);
-      float zv[kTP][4];
+      float zv[kTP][kRowsPer];
 #pragma unroll
       for (int i = 0; i < kTP; ++i)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int r = 4 * pc[i] + q;
+        for (int q = 0; q < kRowsPer; ++q) {
+          const int r = kRowsPer * pc[i] + q;
           zv[i][q] = (pm[i] >= 0 && r < rows) ? rw[pbox[i] * (kBoxBytes / 4) + r * 128 + pm[i]] : 0.f;
         }
 #pragma unroll
       for (int i = 0; i < kTP; ++i) {
         if (pm[i] < 0) continue;
-        unsigned char* hi = ops + (st * 4 + 2 * pbox[i]) * kOpBytes;
-        unsigned char* lo = hi + kOpBytes;
-        float h4[4], l4[4];
+        unsigned char* hi = ops + (st * 2 * NT + NT * pbox[i]) * kOp;
+        unsigned char* lo = hi + kOp;
+        if constexpr (BF) {
+          uint32_t t2[3][4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float h = __uint_as_float(__float_as_uint(zv[i][q]) & 0xFFFFE000u);
-          h4[q] = h;
-          l4[q] = diag ? 2.f * (zv[i][q] - h) : zv[i][q] - h;
+          for (int q = 0; q < 4; ++q) {
+            uint32_t t0[3], t1[3];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const float z = zv[i][2 * q + h];
+              const __nv_bfloat16 b0 = __float2bfloat16_rn(z);
+              const float r1 = z - __bfloat162float(b0);
+              const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+              const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+              uint32_t* t = h ? t1 : t0;
+              t[0] = __bfloat16_as_ushort(b0);
+              t[1] = __bfloat16_as_ushort(b1);
+              t[2] = __bfloat16_as_ushort(b2);
+            }
+#pragma unroll
+            for (int u = 0; u < 3; ++u) t2[u][q] = t0[u] | (t1[u] << 16);
+          }
+#pragma unroll
+          for (int u = 0; u < 3; ++u)
+            *reinterpret_cast<uint4*>(hi + u * kOp + poff[i]) = make_uint4(t2[u][0], t2[u][1], t2[u][2], t2[u][3]);
+        } else {
+          float h4[4], l4[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float h = __uint_as_float(__float_as_uint(zv[i][q]) & 0xFFFFE000u);
+            h4[q] = h;
+            l4[q] = diag ? 2.f * (zv[i][q] - h) : zv[i][q] - h;
+          }
+          *reinterpret_cast<float4*>(hi + poff[i]) = make_float4(h4[0], h4[1], h4[2], h4[3]);
+          *reinterpret_cast<float4*>(lo + poff[i]) = make_float4(l4[0], l4[1], l4[2], l4[3]);
         }
-        *reinterpret_cast<float4*>(hi + poff[i]) = make_float4(h4[0], h4[1], h4[2], h4[3]);
-        *reinterpret_cast<float4*>(lo + poff[i]) = make_float4(l4[0], l4[1], l4[2], l4[3]);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -523,17 +588,29 @@ __global__ void __launch_bounds__(kThreads, 1) k_gram_tiles(const __grid_constan
       asm volatile("tcgen05.fence::after_thread_sync;");
       const int G = b / kDrainEvery;
       const uint32_t dacc = tmem + (uint32_t)((G & 1) * 128);
-      const uint64_t hI = sdesc_sw128(smem_u32(ops + (st * 4 + 0) * kOpBytes));
-      const uint64_t lI = sdesc_sw128(smem_u32(ops + (st * 4 + 1) * kOpBytes));
-      const uint64_t hJ = diag ? hI : sdesc_sw128(smem_u32(ops + (st * 4 + 2) * kOpBytes));
-      const uint64_t lJ = diag ? lI : sdesc_sw128(smem_u32(ops + (st * 4 + 3) * kOpBytes));
+      auto desc = [&](int t) {
+        return BF ? sdesc_sw64(smem_u32(ops + (st * 2 * NT + t) * kOp)) : sdesc_sw128(smem_u32(ops + (st * 2 * NT + t) * kOp));
+      };
+      const uint64_t aI0 = desc(0), aI1 = desc(1), aI2 = BF ? desc(2) : 0;
+      const uint64_t aJ0 = diag ? aI0 : desc(NT), aJ1 = diag ? aI1 : desc(NT + 1), aJ2 = BF ? (diag ? aI2 : desc(NT + 2)) : 0;
       const bool first = (b % kDrainEvery) == 0;
+      // 32 bytes of K per instruction: 8 TF32 or 16 BF16 values
+      constexpr int kSteps = BF ? kBatch / 16 : kBatch / 8;
 #pragma unroll
-      for (int s2 = 0; s2 < kBatch / 8; ++s2) {
+      for (int s2 = 0; s2 < kSteps; ++s2) {
         const uint64_t k = (uint64_t)(2 * s2);
-        mma_tf32(dacc, hI + k, hJ + k, idesc, (first && s2 == 0) ? 0u : 1u);
-        mma_tf32(dacc, hI + k, lJ + k, idesc, 1u);
-        if (!diag) mma_tf32(dacc, lI + k, hJ + k, idesc, 1u);
+        if constexpr (BF) {
+          mma_bf16(dacc, aI0 + k, aJ0 + k, idesc, (first && s2 == 0) ? 0u : 1u);
+          mma_bf16(dacc, aI0 + k, aJ1 + k, idesc, 1u);
+          mma_bf16(dacc, aI1 + k, aJ0 + k, idesc, 1u);
+          mma_bf16(dacc, aI0 + k, aJ2 + k, idesc, 1u);
+          mma_bf16(dacc, aI2 + k, aJ0 + k, idesc, 1u);
+          mma_bf16(dacc, aI1 + k, aJ1 + k, idesc, 1u);
+        } else {
+          mma_tf32(dacc, aI0 + k, aJ0 + k, idesc, (first && s2 == 0) ? 0u : 1u);
+          mma_tf32(dacc, aI0 + k, aJ1 + k, idesc, 1u);
+          if (!diag) mma_tf32(dacc, aI1 + k, aJ0 + k, idesc, 1u);
+        }
       }
       mma_commit(&op_free[st]);
       if ((b % kDrainEvery) == kDrainEvery - 1 || b == nb - 1) mma_commit(&acc_done[G & 1]);
@@ -591,8 +668,10 @@ __global__ void k_gram_tiles_reduce(const float* __restrict__ Wpart, int npairs,
   }
 }
 
-size_t tiles_smem_bytes() {
-  return 1024 + (size_t)8 * kOpBytes + (size_t)kTileRaw * 2 * kBoxBytes + (size_t)8 * (kTileRaw + 4) + 16;
+size_t tiles_smem_bytes(bool bf) {
+  // operands: 2 stages x 2 boxes x (3 BF16 tiles of 8 KB | 2 TF32 tiles of 16 KB)
+  return 1024 + (size_t)4 * (bf ? 3 * kOpBytes / 2 : 2 * kOpBytes) + (size_t)kTileRaw * 2 * kBoxBytes +
+         (size_t)8 * (kTileRaw + 4) + 16;
 }
 
 size_t smem_bytes(int Khat) {
@@ -605,7 +684,7 @@ bool tk_gram_tc_supported(int Khat) {
   return Khat >= 8 && Khat <= 128 && Khat % 4 == 0 && smem_bytes(Khat) <= 225 * 1024;
 }
 
-bool tk_gram_tiles_supported(int Khat) { return Khat > 128 && Khat <= TK_MAXKHAT && Khat % 4 == 0; }
+bool tk_gram_tiles_supported(int Khat) { return Khat >= 8 && Khat <= TK_MAXKHAT && Khat % 4 == 0; }
 
 int tk_gram_tiles_pairs(int Khat) {
   const int nt = (int)tk_ceil_div(Khat, 128);
@@ -638,7 +717,8 @@ EncodeTiledFn encode_fn() {
 // W (FP64) = Z^T Z for Khat > 128 by 128 x 128 blocks; Wpart holds
 // tk_gram_tiles_splits x tk_gram_tiles_pairs tiles of 128 x 128 floats, pairs
 // the (I, J) block list (device, filled here once).
-void tk_gram_tiles(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, int2* pairs, double* W, cudaStream_t s) {
+void tk_gram_tiles(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart, int2* pairs, double* W, bool bf16,
+                   cudaStream_t s) {
   const int nt = (int)tk_ceil_div(Khat, 128);
   const int np = tk_gram_tiles_pairs(Khat);
   std::vector<int2> hp;
@@ -666,10 +746,12 @@ void tk_gram_tiles(tucker_ctx* c, const float* Z, int R, int Khat, float* Wpart,
   a.cap = c->wait_cap;
   static bool attr = false;
   if (!attr) {
-    TK_CUDA(cudaFuncSetAttribute(k_gram_tiles, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles_smem_bytes()));
+    TK_CUDA(cudaFuncSetAttribute(k_gram_tiles<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles_smem_bytes(false)));
+    TK_CUDA(cudaFuncSetAttribute(k_gram_tiles<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tiles_smem_bytes(true)));
     attr = true;
   }
-  k_gram_tiles<<<nsplit * np, kThreads, tiles_smem_bytes(), s>>>(tm, a);
+  if (bf16) k_gram_tiles<true><<<nsplit * np, kThreads, tiles_smem_bytes(true), s>>>(tm, a);
+  else k_gram_tiles<false><<<nsplit * np, kThreads, tiles_smem_bytes(false), s>>>(tm, a);
   TK_CUDA(cudaGetLastError());
   dim3 g2(16, np);
   k_gram_tiles_reduce<<<g2, 256, 0, s>>>(Wpart, np, nsplit, pairs, Khat, W);

@@ -313,12 +313,16 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
   const int jb = g % a.NB, o = g / a.NB;
   const int j0 = jb * a.TB;
   const int tb = EB ? MB : min(a.TB, a.KB - j0);
+  // outer modes: loops run to the compile-time bound NQ with a runtime guard,
+  // so that every per-mode array stays in registers
+  const int nq_rt = a.nother - 2;
   int oc[NQ];
   if (OUTER) {
     int t = o;
-    for (int q = 2; q < a.nother; ++q) {
-      oc[q - 2] = t % a.Kf[q];
-      t /= a.Kf[q];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      oc[q] = q < nq_rt ? t % a.Kf[q + 2] : 0;
+      if (q < nq_rt) t /= a.Kf[q + 2];
     }
   }
   const int colbase = a.KA * j0 + a.KA * a.KB * o;
@@ -365,8 +369,10 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
     const int64_t sl = slot(k);
     nla[d] = ld_stream(a.oidx[0] + sl, pf);
     nlb[d] = twob ? ld_stream(a.oidx[1] + sl, pf) : 0;
-    if (OUTER)
-      for (int q = 2; q < a.nother; ++q) nq[d][q - 2] = ld_stream(a.oidx[q] + sl, pf);
+    if (OUTER) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) nq[d][q] = q < nq_rt ? ld_stream(a.oidx[q + 2] + sl, pf) : 0;
+    }
   };
   // rows of the element whose stream sits in slot d (D ahead of use); an
   // exact FP32 row whose length is 2 mod 4 ends with an 8-byte load
@@ -409,8 +415,11 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
         }
       }
     }
-    if (OUTER)
-      for (int q = 2; q < a.nother; ++q) fq[d][q - 2] = __ldg(a.F[q] + (int64_t)nq[d][q - 2] * a.ld[q] + oc[q - 2]);
+    if (OUTER) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        fq[d][q] = q < nq_rt ? __ldg(a.F[q + 2] + (int64_t)nq[d][q] * a.ld[q + 2] + oc[q]) : T(1);
+    }
   };
 
 #pragma unroll
@@ -436,8 +445,10 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
           cur = cd;
         }
         T vc = v[d];
-        if (OUTER)
-          for (int q = 2; q < a.nother; ++q) vc *= fq[d][q - 2];
+        if (OUTER) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) vc *= fq[d][q];
+        }
 #pragma unroll
         for (int jj = 0; jj < MB; ++jj) {
           const T t = vc * (twob ? B[d][jj] : T(jj == 0));

@@ -18,6 +18,10 @@ LIB_PATH = os.path.join(_HERE, "libtucker.so")
 
 TUCKER_FP32 = 0
 TUCKER_FP64 = 1
+TUCKER_BF16X3 = 2
+# context precision names: FP32 values with the Gram in split TF32 ("fp32" =
+# "tf32x3") or split BF16 ("bf16x3"), or plain FP64
+PREC = {"fp32": TUCKER_FP32, "tf32x3": TUCKER_FP32, "bf16x3": TUCKER_BF16X3, "fp64": TUCKER_FP64}
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NUMERIC", 5: "ERR_TIMEOUT",
           6: "ERR_STATE", 7: "ERR_INDEX"}
 PHASES = ("ttm_chain", "fixup", "gram", "eig", "backproj_cholqr2", "core_fit", "adjoint", "other")
@@ -133,7 +137,7 @@ class Tucker:
     """One COO tensor prepared for the HOOI hot path (wraps a tucker_t).
 
     idx  : (N, nnz) int32 CUDA tensor of 0-based coordinates (distinct)
-    vals : (nnz,) float32 (prec="fp32") or float64 (prec="fp64") CUDA tensor
+    vals : (nnz,) float32 (prec "fp32", "tf32x3" or "bf16x3") or float64 (prec="fp64") CUDA tensor
     L, K : mode lengths and core lengths
     """
 
@@ -145,8 +149,10 @@ class Tucker:
         self.N = len(L)
         self.L = tuple(int(x) for x in L)
         self.K = tuple(int(x) for x in K)
+        if prec not in PREC:
+            raise ValueError(f"prec must be one of {sorted(PREC)}")
         self.prec = prec
-        self.dtype = torch.float32 if prec == "fp32" else torch.float64
+        self.dtype = torch.float64 if prec == "fp64" else torch.float32
         _need_cuda(idx, torch.int32, "idx")
         _need_cuda(vals, self.dtype, "vals")
         if idx.dim() != 2 or idx.shape[0] != self.N or vals.shape != (idx.shape[1],):
@@ -154,7 +160,7 @@ class Tucker:
         self.nnz = int(vals.shape[0])
         opts = Opts()
         self.lib.tucker_default_opts(ctypes.byref(opts))
-        opts.prec = TUCKER_FP32 if prec == "fp32" else TUCKER_FP64
+        opts.prec = PREC[prec]
         opts.P_bins = int(P_bins)
         opts.gauss_seidel = int(bool(gauss_seidel))
         opts.timing = int(bool(timing))

@@ -7,8 +7,8 @@ from oracle import tucker_oracle as O
 from paper_1804_09494_gb300 import synth
 from paper_1804_09494_gb300.tucker import Tucker
 
-DT = {"fp32": torch.float32, "fp64": torch.float64}
-NP = {"fp32": np.float32, "fp64": np.float64}
+DT = {"fp32": torch.float32, "bf16x3": torch.float32, "fp64": torch.float64}
+NP = {"fp32": np.float32, "bf16x3": np.float32, "fp64": np.float64}
 # relative Frobenius tolerance of the TTM-chain: FP32 per the method's
 # acceptance bound; FP64 from ~1e3 rounding steps of 1.1e-16
 TTM_TOL = {"fp32": 1e-5, "fp64": 1e-12}
