@@ -95,7 +95,10 @@ typedef struct {
                           * -1 = abandon every such wait at once (fault injection: runs   *
                           * the timeout path -- copies and MMAs in flight are still       *
                           * awaited -- with no stuck wait)                                */
-  int32_t reserved0;     /* must be zero                                                  */
+  int32_t ttm_path;      /* 0 = the tensor-core TTM-chain where it applies (4-mode FP32   *
+                          * contexts with 32 <= K_a K_b <= 128, K_c <= 48, Khat >= 256,    *
+                          * a < b < c the other modes; it keeps a second, block-padded     *
+                          * copy of those modes' elements), 1 = CUDA cores only           */
   tucker_alloc_fn alloc; /* NULL: the library calls cudaMalloc / cudaFree itself          */
   tucker_free_fn free;   /* must be non-NULL exactly when alloc is                        */
   void* alloc_user;      /* passed to alloc and free                                      */
@@ -137,6 +140,16 @@ void tucker_destroy(tucker_t t);
 
 /* Message of the last error on this context (or of the last failed init when t is NULL). */
 const char* tucker_last_error(tucker_t t);
+
+/*
+ * tucker_ttm_form -- which TTM-chain form mode `mode` uses (Section 3, eq. (1)):
+ * *tensor_cores = 1 for the tensor-core form (tcgen05 MMAs over 8-element
+ * blocks of a slice; see tucker_opts.ttm_path), 0 for the CUDA-core form;
+ * *blocks = the 8-element blocks of that mode's padded copy (elements plus
+ * padding, / 8), 0 for the CUDA-core form.  Either output may be NULL.
+ * Host-only.
+ */
+tucker_status tucker_ttm_form(tucker_t t, int mode, int32_t* tensor_cores, int64_t* blocks);
 
 /*
  * tucker_stats -- Section 4.1 metrics of the mode-n Lite partition and the

@@ -220,7 +220,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
       tk_throw(TUCKER_ERR_ARG, "unknown precision");
     if (o.P_bins < 0) tk_throw(TUCKER_ERR_ARG, "P_bins must be >= 0");
     if (o.wait_cap < -1) tk_throw(TUCKER_ERR_ARG, "wait_cap must be >= -1");
-    if (o.reserved0) tk_throw(TUCKER_ERR_ARG, "reserved option fields must be zero");
+    if (o.ttm_path != 0 && o.ttm_path != 1) tk_throw(TUCKER_ERR_ARG, "ttm_path must be 0 or 1");
     for (int i = 0; i < 4; ++i)
       if (o.reserved[i]) tk_throw(TUCKER_ERR_ARG, "reserved option fields must be zero");
     if ((o.alloc == nullptr) != (o.free == nullptr)) tk_throw(TUCKER_ERR_ARG, "alloc and free must be set together");
@@ -237,6 +237,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     c->gram_bf16 = o.prec == TUCKER_BF16X3;
     c->esz = c->prec == TUCKER_FP32 ? 4 : 8;
     c->gauss_seidel = o.gauss_seidel != 0;
+    c->ttm_path = o.ttm_path;
     c->timing = o.timing != 0;
     c->wait_cap = o.wait_cap;
     c->sm_count = tk_sm_count();
@@ -282,6 +283,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
         P = (int)p;
       }
       tk_partition_mode(c, n, d_idx, d_val, P, s);
+      if (c->ttm_path == 0 && tk_ttmc_tc_eligible(c, n)) tk_ttmc_tc_build(c, n, s);
       const tk_mode& md = c->mode[n];
       if (K[n] > md.R || K[n] > md.Khat)
         tk_throw(TUCKER_ERR_ARG, "K_" + std::to_string(n) + " exceeds min(non-empty slices, prod of the other K)");
@@ -351,6 +353,16 @@ tucker_status tucker_stats(tucker_t t, int mode, int64_t* E_max, int64_t* R_sum,
     if (R_max) *R_max = md.R_max;
     if (R_n) *R_n = md.R;
     if (P) *P = md.P;
+  });
+}
+
+tucker_status tucker_ttm_form(tucker_t t, int mode, int32_t* tensor_cores, int64_t* blocks) {
+  return guarded(t, [&] {
+    check_ctx(t);
+    check_mode(t, mode);
+    const tk_mode& md = t->mode[mode];
+    if (tensor_cores) *tensor_cores = md.tc ? 1 : 0;
+    if (blocks) *blocks = md.tc ? md.tc_nblk : 0;
   });
 }
 

@@ -65,6 +65,17 @@ struct tk_mode {
   int32_t* chunk_b0 = nullptr;     // nchunks (inclusive)
   int32_t* chunk_b1 = nullptr;     // nchunks (exclusive)
   int32_t* split_chunk0 = nullptr; // nsplit + 1
+  // tensor-core TTM-chain copy (4-mode FP32 contexts with a large Khat, tk_ttmc_tc.cu):
+  // bins contiguous, each segment padded to 8-element blocks
+  bool tc = false;
+  int tc_Mu = 0, tc_Nu = 0;        // A rows K_a K_b, B rows K_c
+  int64_t tc_nblk = 0;
+  int64_t* tc_blk_ptr = nullptr;   // Pa + 1: first block of each bin
+  uint32_t* tc_code = nullptr;     // nblk: compact row, or 2^31 | (2 bin + head) for a split piece
+  uint8_t* tc_flag = nullptr;      // nblk: 1 = first block of its segment, 2 = last
+  int32_t* tc_oidx[3] = {};        // 8 nblk each
+  float* tc_val = nullptr;         // 8 nblk (0 on padding)
+  int32_t* tc_perm = nullptr;      // 8 nblk (-1 on padding)
 };
 
 struct tk_buf {
@@ -102,6 +113,7 @@ struct tucker_ctx {
   bool gram_bf16 = false;   // TUCKER_BF16X3: the Gram in split BF16
   size_t esz = 4;
   int gauss_seidel = 0;
+  int ttm_path = 0;         // 0: tensor-core TTM-chain where eligible, 1: CUDA cores only
   int timing = 0;
   int sm_count = 0;
   double normT2 = 0.0;
@@ -146,7 +158,9 @@ struct tucker_ctx {
   // adjoint workspace (allocated by the first ttm_chain_backward call)
   bool bwd_ready = false;
   int32_t* bwd_pos[TK_MAXN] = {};  // nnz: slot of element e in mode m's copy
-  void* bwd_X = nullptr;           // max_m cap_m * K_m: per-slot contributions to dF_m
+  void* bwd_X = nullptr;           // per-slot contributions to dF of the targets of one element pass
+                                   // (slot order of the TTM-chain mode's copy)
+  void* bwd_dv = nullptr;          // max_n cap_n: dval in slot order
   void* bwd_Zc = nullptr;          // max_m R_m * K_m: compact dF_m
   void* bwd_Zp = nullptr;          // max_m 2 * Pa_m * K_m: split-piece partials
   double* bwd_Zch = nullptr;       // max_m nchunks_m * K_m: fix-up chunk sums
@@ -205,6 +219,12 @@ int tk_ttmc_groups(const tucker_ctx* c, int n);
 int tk_ttmc_threads_per_sm(const tucker_ctx* c, int n);
 void tk_ttmc_forward(tucker_ctx* c, int n, void* const* F, const int* ldF, const void* vals_override, void* Z,
                      cudaStream_t s);
+// tensor-core form (tk_ttmc_tc.cu): 4-mode FP32 contexts with 32 <= K_a K_b <= 128,
+// K_c <= 48 and Khat >= 256 (a < b < c the modes other than n)
+bool tk_ttmc_tc_eligible(const tucker_ctx* c, int n);
+void tk_ttmc_tc_build(tucker_ctx* c, int n, cudaStream_t s);
+void tk_ttmc_tc_launch(tucker_ctx* c, int n, void* const* F, const int* ldF, const void* vals_override, void* Z,
+                       cudaStream_t s);
 void tk_ttmc_backward(tucker_ctx* c, int n, void* const* F, const int* ldF, const void* dZ,
                       const void* vals_override, void* const* dF, void* dval, cudaStream_t s);
 

@@ -463,21 +463,32 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
   if (len > 0) flush_clear(cur, 1);
 }
 
+// Outputs of one element pass of the adjoint, all in the slot order of mode
+// n's copy (slot s = the element's position in that copy):
+//   dv[s]           dval of the element (scattered to original order at the end)
+//   X[q][s * K_q]   its contribution to dF of the q-th other mode
+// A null pointer skips that output; first != 0: the pass writes, else adds.
+template <typename T>
+struct BwdOut {
+  T* dv;
+  int first_dv;
+  T* X[TK_MAXN - 1];
+  int first[TK_MAXN - 1];
+};
+
 // Adjoint, element pass over mode n's copy for one column group g (groups are
 // launched one after another, in order).  A thread walks its bin, stages the
 // cotangent row dZ[row] of each slice once, and for every element computes
-//     dval(e) += so * <fa, D fb>                     (so: outer-mode scalings)
-// and the element's contribution to dF of the target mode m:
-//     m = a:     X[pos_m(e)][i]        (+)= w so sum_j D[i,j] fb[j]
-//     m = b:     X[pos_m(e)][j0 + j]   (+)= w so sum_i D[i,j] fa[i]
-//     m = outer: X[pos_m(e)][oc_m]     (+)= w <fa, D fb> prod_{q != m} F_q[l_q][oc_q]
-// where pos_m(e) is the element's slot in mode m's copy: every slot is
-// written by exactly one thread per launch, so there are no atomics and the
-// order of the sums is fixed.  target < 0: dval only.
+//     dv(e) (+)= so * <fa, D fb>                     (so: outer-mode scalings)
+// and the element's contributions to dF of the other modes:
+//     mode a:     X_a[s][i]        (+)= w so sum_j D[i,j] fb[j]
+//     mode b:     X_b[s][j0 + j]   (+)= w so sum_i D[i,j] fa[i]
+//     outer q:    X_q[s][oc_q]      += w <fa, D fb> prod_{q2 != q} F_q2[l_q2][oc_q2]
+// Every slot is written by exactly one thread per launch, the 32 threads of a
+// warp write consecutive slots (coalesced rows), there are no atomics and the
+// order of the sums is fixed; the reduction to dF_m gathers X by slot.
 template <typename T, int MA, int MB, bool EA, bool EB>
-__global__ void __launch_bounds__(128) k_bwd_elem(const TtmcArgs<T> a, int g, int target, int first_dval,
-                                                  int first_x, const int32_t* __restrict__ pos, int Km,
-                                                  T* __restrict__ X) {
+__global__ void __launch_bounds__(128) k_bwd_elem(const TtmcArgs<T> a, int g, const BwdOut<T> out) {
   extern __shared__ __align__(16) char smem[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t bw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -566,27 +577,32 @@ __global__ void __launch_bounds__(128) k_bwd_elem(const TtmcArgs<T> a, int g, in
       T dot = T(0);
 #pragma unroll
       for (int i = 0; i < MA; ++i) dot = fma(fa[i], x[i], dot);
-      if (a.dval) {
-        T* dv = a.dval + e;
-        *dv = first_dval ? so * dot : *dv + so * dot;
+      const int64_t slot = (wbase + (int64_t)c * C + j) * 32 + lane;
+      if (out.dv) {
+        T* dv = out.dv + slot;
+        *dv = out.first_dv ? so * dot : *dv + so * dot;
       }
-      if (target >= 0) {
-        T* xr = X + (int64_t)pos[e] * Km;
-        const T ws = w * so;
-        if (target == 0) {
+      const T ws = w * so;
+      if (out.X[0]) {
+        T* xr = out.X[0] + slot * a.KA;
+        const bool f = out.first[0] != 0;
 #pragma unroll
-          for (int i = 0; i < MA; ++i)
-            if (EA || i < ka) xr[i] = first_x ? ws * x[i] : xr[i] + ws * x[i];
-        } else if (target == 1) {
+        for (int i = 0; i < MA; ++i)
+          if (EA || i < ka) xr[i] = f ? ws * x[i] : xr[i] + ws * x[i];
+      }
+      if (a.nother >= 2 && out.X[1]) {
+        T* xr = out.X[1] + slot * a.KB + j0;
+        const bool f = out.first[1] != 0;
 #pragma unroll
-          for (int jj = 0; jj < MB; ++jj)
-            if (EB || jj < tb) xr[j0 + jj] = first_x ? ws * y[jj] : xr[j0 + jj] + ws * y[jj];
-        } else {
-          T prod = w * dot;
-          for (int q2 = 2; q2 < a.nother; ++q2)
-            if (q2 != target) prod *= fq[q2 - 2];
-          xr[oc[target - 2]] += prod;
-        }
+        for (int jj = 0; jj < MB; ++jj)
+          if (EB || jj < tb) xr[jj] = f ? ws * y[jj] : xr[jj] + ws * y[jj];
+      }
+      for (int q = 2; q < a.nother; ++q) {
+        if (!out.X[q]) continue;
+        T prod = w * dot;
+        for (int q2 = 2; q2 < a.nother; ++q2)
+          if (q2 != q) prod *= fq[q2 - 2];
+        out.X[q][slot * a.Kf[q] + oc[q - 2]] += prod;
       }
     }
     __syncwarp();
@@ -597,11 +613,15 @@ __global__ void __launch_bounds__(128) k_bwd_elem(const TtmcArgs<T> a, int g, in
 }
 
 // Adjoint, reduction over mode m's copy: every slice of mode m sums the
-// contributions X[slot] of its elements in slot order (a thread per Lite bin,
-// registers); whole slices write their compact row of Zc, split pieces the
-// bin's partial slots, which the fix-up adds in bin order.
+// contributions of its elements in the order of its copy (a thread per Lite
+// bin, registers).  The contributions were written in the slot order of mode
+// n's copy, so element e = perm_m[slot] reads row pos_n[e] of X.  Whole slices
+// write their compact row of Zc, split pieces the bin's partial slots, which
+// the fix-up adds in bin order.
 template <typename T, int KM>
-__global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int Km, const uint32_t* __restrict__ rowcode,
+__global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int Km, const int32_t* __restrict__ perm,
+                                                    const int32_t* __restrict__ pos_n,
+                                                    const uint32_t* __restrict__ rowcode,
                                                     const int32_t* __restrict__ bin_len, int Pa, int limit,
                                                     T* __restrict__ Zc, T* __restrict__ Zpart) {
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
@@ -629,10 +649,10 @@ __global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int
       for (int q = 0; q < KM; ++q) acc[q] = T(0);
       cur = code;
     }
-    const T* xr = X + sl * Km;
+    const T* xr = X + (int64_t)__ldg(pos_n + __ldg(perm + sl)) * Km;
 #pragma unroll
     for (int q = 0; q < KM; ++q)
-      if (q < Km) acc[q] += xr[q];
+      if (q < Km) acc[q] += __ldg(xr + q);
   }
   if (len > 0) flush(cur);
 }
@@ -646,6 +666,21 @@ __global__ void k_add_rows(const T* __restrict__ Zc, int R, int Km, const int32_
     const int64_t r = i / Km;
     const int k = (int)(i - r * Km);
     dF[(int64_t)row_id[r] * Km + k] += Zc[i];
+  }
+}
+
+// dval[perm[slot]] = dv[slot] for the occupied slots of mode n's copy
+template <typename T>
+__global__ void k_dv_scatter(const T* __restrict__ dv, const int32_t* __restrict__ perm,
+                             const int32_t* __restrict__ bin_len, int Pa, int limit, T* __restrict__ dval) {
+  const int64_t cap = (int64_t)Pa * limit;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t slot = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; slot < cap; slot += stride) {
+    const int lane = (int)(slot & 31);
+    const int64_t rest = slot >> 5;
+    const int64_t k = rest % limit;
+    const int p = (int)((rest / limit) * 32 + lane);
+    if (k < bin_len[p]) dval[perm[slot]] = dv[slot];
   }
 }
 
@@ -767,7 +802,7 @@ KernelT<double> fwd_kernel<double>(int id, bool outer, bool ovr) {
 }
 #undef TK_FWD_PICK
 template <typename T>
-using BwdKernelT = void (*)(TtmcArgs<T>, int, int, int, int, const int32_t*, int, T*);
+using BwdKernelT = void (*)(TtmcArgs<T>, int, BwdOut<T>);
 template <typename T>
 BwdKernelT<T> bwd_kernel(int id);
 template <>
@@ -882,8 +917,12 @@ void forward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const vo
                 ((pl.KA * pl.tile.MB) % VecT<T>::W == 0);
   a.texB = pl.nother >= 2 ? tk_factor_tex(c, F[pl.others[1]]) : 0;
   tk_phase_begin(c, PH_TTM, s);
-  fwd_kernel<T>(pl.tile_id, pl.nother > 2, vals_override != nullptr)<<<blocks_for(md, pl.G), 128, 0, s>>>(a);
-  TK_CUDA(cudaGetLastError());
+  if (md.tc) {
+    tk_ttmc_tc_launch(c, n, F, ldF, vals_override, Z, s);
+  } else {
+    fwd_kernel<T>(pl.tile_id, pl.nother > 2, vals_override != nullptr)<<<blocks_for(md, pl.G), 128, 0, s>>>(a);
+    TK_CUDA(cudaGetLastError());
+  }
   tk_phase_end(c, s);
   tk_launched(c, PH_TTM);
   if (md.nsplit > 0) {
@@ -900,19 +939,46 @@ void forward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const vo
   }
 }
 
+// Sets of other modes whose dF contributions one element pass produces
+// together: both for a 3-mode tensor, one at a time above (the per-slot
+// contribution buffers grow with the number of targets).
+int bwd_sets(int nother, int (*sets)[TK_MAXN - 1], int* sizes) {
+  if (nother <= 2) {
+    for (int q = 0; q < nother; ++q) sets[0][q] = q;
+    sizes[0] = nother;
+    return 1;
+  }
+  for (int q = 0; q < nother; ++q) {
+    sets[q][0] = q;
+    sizes[q] = 1;
+  }
+  return nother;
+}
+
 // Adjoint workspace, allocated by the first backward call of a context:
-// element slots of every mode's copy, the per-slot contributions X, the
-// compact reduction result and the fix-up scratch.
+// element slots of every mode's copy, the per-slot dval and contribution
+// buffers (slot order of the TTM-chain mode's copy), the compact reduction
+// result and the fix-up scratch.
 void ensure_bwd_workspace(tucker_ctx* c, cudaStream_t s) {
   if (c->bwd_ready) return;
   c->alloc_stream = s;
-  int64_t xcap = 0, zc = 0, zp = 0, zch = 0;
-  for (int m = 0; m < c->N; ++m) {
-    const tk_mode& md = c->mode[m];
-    xcap = std::max(xcap, md.cap * (int64_t)c->K[m]);
-    zc = std::max(zc, (int64_t)md.R * c->K[m]);
-    zp = std::max(zp, (int64_t)2 * md.Pa * c->K[m]);
-    zch = std::max(zch, (int64_t)md.nchunks * c->K[m]);
+  int64_t xcap = 0, dvcap = 0, zc = 0, zp = 0, zch = 0;
+  for (int n = 0; n < c->N; ++n) {
+    const tk_mode& md = c->mode[n];
+    int others[TK_MAXN - 1], no = 0;
+    for (int m = 0; m < c->N; ++m)
+      if (m != n) others[no++] = m;
+    int sets[TK_MAXN - 1][TK_MAXN - 1], sizes[TK_MAXN - 1];
+    const int ns = bwd_sets(no, sets, sizes);
+    for (int t = 0; t < ns; ++t) {
+      int64_t k = 0;
+      for (int i = 0; i < sizes[t]; ++i) k += c->K[others[sets[t][i]]];
+      xcap = std::max(xcap, md.cap * k);
+    }
+    dvcap = std::max(dvcap, md.cap);
+    zc = std::max(zc, (int64_t)md.R * c->K[n]);
+    zp = std::max(zp, (int64_t)2 * md.Pa * c->K[n]);
+    zch = std::max(zch, (int64_t)md.nchunks * c->K[n]);
   }
   for (int m = 0; m < c->N; ++m) {
     const tk_mode& md = c->mode[m];
@@ -921,24 +987,29 @@ void ensure_bwd_workspace(tucker_ctx* c, cudaStream_t s) {
                                                                                          md.limit, c->bwd_pos[m]);
     TK_CUDA(cudaGetLastError());
   }
-  c->bwd_X = tk_alloc(c, (size_t)xcap * c->esz);
+  c->bwd_X = tk_alloc(c, (size_t)std::max<int64_t>(xcap, 1) * c->esz);
+  c->bwd_dv = tk_alloc(c, (size_t)std::max<int64_t>(dvcap, 1) * c->esz);
   c->bwd_Zc = tk_alloc(c, (size_t)std::max<int64_t>(zc, 1) * c->esz);
   c->bwd_Zp = tk_alloc(c, (size_t)std::max<int64_t>(zp, 1) * c->esz);
   c->bwd_Zch = (double*)tk_alloc(c, (size_t)std::max<int64_t>(zch, 1) * 8);
   c->bwd_ready = true;
 }
 
+// dF_m += the contributions X (slot order of mode n's copy, rows of K_m)
 template <typename T>
-void reduce_into(tucker_ctx* c, int m, T* dF, cudaStream_t s) {
+void reduce_into(tucker_ctx* c, int m, int n, const T* X, T* dF, cudaStream_t s) {
   tk_mode& md = c->mode[m];
   const int Km = c->K[m];
-  const T* X = (const T*)c->bwd_X;
+  const int32_t* pos_n = c->bwd_pos[n];
   T* Zc = (T*)c->bwd_Zc;
   T* Zp = (T*)c->bwd_Zp;
   const unsigned grid = (unsigned)tk_ceil_div(md.Pa, 128);
-  if (Km <= 8) k_bwd_reduce<T, 8><<<grid, 128, 0, s>>>(X, Km, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
-  else if (Km <= 16) k_bwd_reduce<T, 16><<<grid, 128, 0, s>>>(X, Km, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
-  else k_bwd_reduce<T, 32><<<grid, 128, 0, s>>>(X, Km, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+  if (Km <= 8)
+    k_bwd_reduce<T, 8><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+  else if (Km <= 16)
+    k_bwd_reduce<T, 16><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+  else
+    k_bwd_reduce<T, 32><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
   TK_CUDA(cudaGetLastError());
   if (md.nsplit > 0) {
     dim3 g1(md.nchunks, (unsigned)tk_ceil_div(Km, 32));
@@ -970,34 +1041,55 @@ void backward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const v
   const unsigned grid = blocks_for(md, 1);
   tk_phase_begin(c, PH_BWD, s);
   ensure_bwd_workspace(c, s);
-  // the element passes of the first target also produce dval; without any
-  // target, dval alone
-  bool dval_done = dval == nullptr;
-  for (int q = 0; q < pl.nother; ++q) {
-    const int m = pl.others[q];
-    if (!dF || !dF[m]) continue;
-    const int Km = c->K[m];
-    if (q >= 2) TK_CUDA(cudaMemsetAsync(c->bwd_X, 0, (size_t)c->mode[m].cap * Km * sizeof(T), s));
-    a.dval = dval_done ? nullptr : (T*)dval;
+  T* Xbase = (T*)c->bwd_X;
+  T* dv = (T*)c->bwd_dv;
+  bool dval_pending = dval != nullptr;
+  auto element_passes = [&](BwdOut<T> o) {
     for (int g = 0; g < pl.G; ++g) {
-      // X of mode a: every group adds to all K_a columns (first group writes);
-      // of mode b: group g owns the column block of jb = g % NB (first outer
-      // combination writes); of an outer mode: zeroed above, always added
-      const int first_x = q == 0 ? g == 0 : (q == 1 ? g < pl.NB : 0);
-      kern<<<grid, 128, shm, s>>>(a, g, q, g == 0, first_x, c->bwd_pos[m], Km, (T*)c->bwd_X);
+      // X of mode a: every group adds to all K_a columns (the first writes);
+      // of mode b: group g owns the column block jb = g % NB (the first outer
+      // combination writes); of an outer mode: zeroed before, always added
+      o.first_dv = g == 0;
+      o.first[0] = g == 0;
+      o.first[1] = g < pl.NB;
+      kern<<<grid, 128, shm, s>>>(a, g, o);
       TK_CUDA(cudaGetLastError());
     }
     tk_launched(c, PH_BWD, pl.G);
-    dval_done = true;
-    reduce_into<T>(c, m, (T*)dF[m], s);
+    if (o.dv) {
+      k_dv_scatter<T><<<(unsigned)std::min<int64_t>(tk_ceil_div(md.cap, 256), 1 << 20), 256, 0, s>>>(
+          dv, md.perm, md.bin_len, md.Pa, md.limit, (T*)dval);
+      TK_CUDA(cudaGetLastError());
+      tk_launched(c, PH_BWD, 1);
+    }
+  };
+  int sets[TK_MAXN - 1][TK_MAXN - 1], sizes[TK_MAXN - 1];
+  const int nsets = bwd_sets(pl.nother, sets, sizes);
+  for (int t = 0; t < nsets; ++t) {
+    BwdOut<T> o{};
+    T* X[TK_MAXN - 1] = {};
+    int64_t off = 0;
+    bool any = false;
+    for (int i = 0; i < sizes[t]; ++i) {
+      const int q = sets[t][i], m = pl.others[q];
+      if (!dF || !dF[m]) continue;
+      X[q] = Xbase + off;
+      off += md.cap * c->K[m];
+      if (q >= 2) TK_CUDA(cudaMemsetAsync(X[q], 0, (size_t)md.cap * c->K[m] * sizeof(T), s));
+      o.X[q] = X[q];
+      any = true;
+    }
+    if (!any) continue;
+    o.dv = dval_pending ? dv : nullptr;
+    element_passes(o);
+    dval_pending = false;
+    for (int q = 0; q < pl.nother; ++q)
+      if (X[q]) reduce_into<T>(c, pl.others[q], n, X[q], (T*)dF[pl.others[q]], s);
   }
-  if (!dval_done) {
-    a.dval = (T*)dval;
-    for (int g = 0; g < pl.G; ++g) {
-      kern<<<grid, 128, shm, s>>>(a, g, -1, g == 0, 0, nullptr, 0, nullptr);
-      TK_CUDA(cudaGetLastError());
-    }
-    tk_launched(c, PH_BWD, pl.G);
+  if (dval_pending) {
+    BwdOut<T> o{};
+    o.dv = dv;
+    element_passes(o);
   }
   tk_phase_end(c, s);
 }

@@ -40,7 +40,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 
 class Opts(ctypes.Structure):
     _fields_ = [("prec", _I32), ("P_bins", _I32), ("gauss_seidel", _I32), ("timing", _I32),
-                ("wait_cap", _I32), ("reserved0", _I32), ("alloc", ALLOC_FN), ("free", FREE_FN),
+                ("wait_cap", _I32), ("ttm_path", _I32), ("alloc", ALLOC_FN), ("free", FREE_FN),
                 ("alloc_user", _VP), ("reserved", _I32 * 4)]
 
 
@@ -72,6 +72,7 @@ SIGNATURES = {
     "tucker_destroy": (None, [_VP]),
     "tucker_last_error": (ctypes.c_char_p, [_VP]),
     "tucker_stats": (ctypes.c_int, [_VP, ctypes.c_int, _P64, _P64, _P64, _P64, _P64]),
+    "tucker_ttm_form": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), _P64]),
     "tucker_partition": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "tucker_partition_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "ttm_chain": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP), _VP, _VP, _VP, _VP]),
@@ -139,10 +140,11 @@ class Tucker:
     idx  : (N, nnz) int32 CUDA tensor of 0-based coordinates (distinct)
     vals : (nnz,) float32 (prec "fp32", "tf32x3" or "bf16x3") or float64 (prec="fp64") CUDA tensor
     L, K : mode lengths and core lengths
+    ttm_path : "auto" (the tensor-core TTM-chain where it applies) or "cuda_cores"
     """
 
     def __init__(self, idx, vals, L, K, prec="fp32", P_bins=0, gauss_seidel=False, timing=False,
-                 wait_cap=0, allocator="torch"):
+                 wait_cap=0, allocator="torch", ttm_path="auto"):
         self.lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("libtucker needs a CUDA device")
@@ -165,6 +167,9 @@ class Tucker:
         opts.gauss_seidel = int(bool(gauss_seidel))
         opts.timing = int(bool(timing))
         opts.wait_cap = int(wait_cap)
+        if ttm_path not in ("auto", "cuda_cores"):
+            raise ValueError('ttm_path must be "auto" or "cuda_cores"')
+        opts.ttm_path = 0 if ttm_path == "auto" else 1
         # device memory from torch's caching allocator (allocator="torch"), or
         # the library's own cudaMalloc (allocator=None); the callbacks live as
         # long as the context
@@ -221,6 +226,12 @@ class Tucker:
         v = [ctypes.c_int64() for _ in range(5)]
         self._check(self.lib.tucker_stats(self.h, mode, *[ctypes.byref(x) for x in v]))
         return dict(zip(("E_max", "R_sum", "R_max", "R_n", "P"), (x.value for x in v)))
+
+    def ttm_form(self, mode):
+        """{"tensor_cores": bool, "blocks": padded 8-element blocks (0 on CUDA cores)}"""
+        tc, nb = ctypes.c_int32(), ctypes.c_int64()
+        self._check(self.lib.tucker_ttm_form(self.h, mode, ctypes.byref(tc), ctypes.byref(nb)))
+        return {"tensor_cores": bool(tc.value), "blocks": nb.value}
 
     def partition(self, mode):
         P = self.stats(mode)["P"]
