@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="a step also runs the adjoint of every mode's TTM-chain (dL/dF_m and dL/dvals for a fixed "
                          "cotangent dZ_n), the differentiable use of the path")
+    ap.add_argument("--schemes", type=int, default=0, metavar="P",
+                    help="instead of timing: print the Section 4.1 metrics (E_max, R_sum, R_max) of Lite, CoarseG "
+                         "and MediumG with P processors for every mode of the workload (the paper's comparison of "
+                         "distribution schemes, Section 7), with seeded random orders")
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16x3"],
                     help="FP32 context with the Gram in split TF32 (fp32) or split BF16 (bf16x3)")
     return ap.parse_args()
@@ -488,9 +492,47 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_schemes(args):
+    """One JSON line: per mode, the metrics of Lite (the context partitioned with
+    P bins), CoarseG and MediumG (device, seeded random orders), and the
+    distribution time of each."""
+    import numpy as np
+    import torch
+
+    from paper_1804_09494_gb300.tucker import Tucker
+
+    w = load_workload(args)
+    L, K, P = w["L"], w["K"], args.schemes
+    idx_d = torch.from_numpy(w["idx"]).cuda()
+    vals_d = torch.from_numpy(w["vals"]).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tk = Tucker(idx_d, vals_d, L, K, prec="fp32", P_bins=P, ttm_path="cuda_cores")
+    torch.cuda.synchronize()
+    t_lite = time.perf_counter() - t0
+    rng = np.random.default_rng(2024)
+    pos = [torch.from_numpy(rng.permutation(l).astype(np.int32)).cuda() for l in L]
+    modes = []
+    for n in range(len(L)):
+        row = {"mode": n, "avg_E": -(-len(w["vals"]) // P), "R_n": tk.stats(n)["R_n"]}
+        st = tk.stats(n)
+        row["lite"] = {k: st[k] for k in ("E_max", "R_sum", "R_max")}
+        for name in ("coarseg", "mediumg"):
+            t0 = time.perf_counter()
+            m = tk.scheme_metrics(n, name, P, pos)
+            row[name] = {k: m[k] for k in ("E_max", "R_sum", "R_max")}
+            row[name]["metrics_s"] = round(time.perf_counter() - t0, 4)
+        modes.append(row)
+    tk.close()
+    print(json.dumps({"workload": args.workload, "nnz": len(w["vals"]), "P": P, "lite_partition_s": round(t_lite, 3),
+                      "modes": modes}))
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.schemes:
+        run_schemes(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -142,6 +142,34 @@ void tucker_destroy(tucker_t t);
 const char* tucker_last_error(tucker_t t);
 
 /*
+ * tucker_scheme_metrics -- the Section 4.1 metrics along `mode` of one of the
+ * prior distribution schemes the paper compares Lite with (Section 5),
+ * computed on the device from the context's tensor, for P processors:
+ *   scheme 1 = CoarseG: every slice whole; the slices in the random order
+ *     d_pos[mode] (d_pos[mode][l] = position of slice l) are cut into
+ *     contiguous blocks balanced by elements: the slice at position t, with
+ *     H_t elements in the slices before it, goes to processor
+ *     floor(P * H_t / nnz);
+ *   scheme 2 = MediumG: a processor grid q_1 x ... x q_N = P (the prime
+ *     factors of P, largest first, each to the mode with the largest L_m / q_m
+ *     so far, the lowest mode on a tie) over the permuted indices d_pos[m][l];
+ *     mode m's positions fall in range floor(x * q_m / L_m); cell
+ *     (b_1, ..., b_N) is processor b_1 + q_1 (b_2 + q_2 (...)).
+ * d_pos: N device pointers to int32 permutations of [0, L_m) (read: d_pos[mode]
+ * for CoarseG, all for MediumG; an out-of-range entry, or for CoarseG a
+ * position given twice, returns TUCKER_ERR_INDEX).  Outputs: E_max = max_p |E^p|, R_sum = sum_p R^p, R_max =
+ * max_p R^p (R^p = distinct mode-`mode` slices among processor p's elements),
+ * on the host (any may be NULL); d_E, d_R: optional device arrays of P int64
+ * receiving E^p and R^p.  MediumG needs L_mode * P / q_mode <= 2^35 (a
+ * presence bit map).  Temporary device memory comes from the context's
+ * callbacks; synchronises `stream`.  The Lite metrics of the context's own
+ * partition are tucker_stats.
+ */
+tucker_status tucker_scheme_metrics(tucker_t t, int mode, int scheme, int P, const int32_t* const* d_pos,
+                                    int64_t* E_max, int64_t* R_sum, int64_t* R_max, int64_t* d_E, int64_t* d_R,
+                                    void* stream);
+
+/*
  * tucker_ttm_form -- which TTM-chain form mode `mode` uses (Section 3, eq. (1)):
  * *tensor_cores = 1 for the tensor-core form (tcgen05 MMAs over 8-element
  * blocks of a slice; see tucker_opts.ttm_path), 0 for the CUDA-core form;

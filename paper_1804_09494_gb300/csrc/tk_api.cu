@@ -356,6 +356,21 @@ tucker_status tucker_stats(tucker_t t, int mode, int64_t* E_max, int64_t* R_sum,
   });
 }
 
+tucker_status tucker_scheme_metrics(tucker_t t, int mode, int scheme, int P, const int32_t* const* d_pos,
+                                    int64_t* E_max, int64_t* R_sum, int64_t* R_max, int64_t* d_E, int64_t* d_R,
+                                    void* stream) {
+  return guarded(t, [&] {
+    check_ctx(t);
+    check_mode(t, mode);
+    int64_t o[3] = {0, 0, 0};
+    tk_scheme_metrics(t, mode, scheme, P, d_pos, o, d_E, d_R, (cudaStream_t)stream);
+    check_device_error(t, (cudaStream_t)stream);
+    if (E_max) *E_max = o[0];
+    if (R_sum) *R_sum = o[1];
+    if (R_max) *R_max = o[2];
+  });
+}
+
 tucker_status tucker_ttm_form(tucker_t t, int mode, int32_t* tensor_cores, int64_t* blocks) {
   return guarded(t, [&] {
     check_ctx(t);

@@ -248,6 +248,13 @@ void tk_factor_update(tucker_ctx* c, int n, const void* Z, void* F_out, int ldF_
                       double* sigma_out, cudaStream_t s);
 void tk_alloc_fuws(tucker_ctx* c, int n);
 
+// ---- prior distribution schemes (tk_schemes.cu) ----
+// Section 4.1 metrics of CoarseG (scheme 1) or MediumG (scheme 2) along mode n:
+// out3 = {E_max, R_sum, R_max} on the host; d_E / d_R (P int64 each, may be
+// NULL) receive E^p and R^p.  Synchronises s.
+void tk_scheme_metrics(tucker_ctx* c, int n, int scheme, int P, const int32_t* const* d_pos, int64_t* out3,
+                       int64_t* d_E, int64_t* d_R, cudaStream_t s);
+
 // ---- core / fit (tk_core.cu) ----
 // New core from the TTM-chain of mode tk_core_mode(c); with before_Fn, the
 // stream waits on that event after the TTM-chain, before F_n is first read.

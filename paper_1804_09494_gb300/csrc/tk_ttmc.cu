@@ -617,8 +617,11 @@ __global__ void __launch_bounds__(128) k_bwd_elem(const TtmcArgs<T> a, int g, co
 // bin, registers).  The contributions were written in the slot order of mode
 // n's copy, so element e = perm_m[slot] reads row pos_n[e] of X.  Whole slices
 // write their compact row of Zc, split pieces the bin's partial slots, which
-// the fix-up adds in bin order.
-template <typename T, int KM>
+// the fix-up adds in bin order.  A bin is one thread's chain of dependent
+// gathers (perm -> pos -> row), so the loop keeps PD elements' rows and the
+// next PD elements' row indices in flight: slot d holds element j + d's row and
+// element j + d + PD's index, refilled right after the element is added.
+template <typename T, int KM, int PD>
 __global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int Km, const int32_t* __restrict__ perm,
                                                     const int32_t* __restrict__ pos_n,
                                                     const uint32_t* __restrict__ rowcode,
@@ -627,6 +630,7 @@ __global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int
   const int bin = blockIdx.x * blockDim.x + threadIdx.x;
   if (bin >= Pa) return;
   const int len = bin_len[bin];
+  if (len == 0) return;
   const int64_t base = (int64_t)(bin >> 5) * limit * 32 + (bin & 31);
   T acc[KM];
 #pragma unroll
@@ -639,22 +643,41 @@ __global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int
     for (int k = 0; k < KM; ++k)
       if (k < Km) dst[k] = acc[k];
   };
+  // element k's slot; past the bin's end the last element is read again (never added)
+  auto slot = [&](int k) __attribute__((always_inline)) { return base + (int64_t)min(k, len - 1) * 32; };
+  auto index_of = [&](int k) __attribute__((always_inline)) { return __ldg(pos_n + __ldg(perm + slot(k))); };
+  T xr[PD][KM];
+  uint32_t cc[PD];
+  int nx[PD];
+  auto load_row = [&](int d, int k, int p) __attribute__((always_inline)) {
+    cc[d] = __ldg(rowcode + slot(k));
+    const T* r = X + (int64_t)p * Km;
+#pragma unroll
+    for (int q = 0; q < KM; ++q) xr[d][q] = q < Km ? __ldg(r + q) : T(0);
+  };
+#pragma unroll
+  for (int d = 0; d < PD; ++d) load_row(d, d, index_of(d));
+#pragma unroll
+  for (int d = 0; d < PD; ++d) nx[d] = index_of(d + PD);
 #pragma unroll 1
-  for (int k = 0; k < len; ++k) {
-    const int64_t sl = base + (int64_t)k * 32;
-    const uint32_t code = rowcode[sl];
-    if (code != cur) {
-      if (cur != 0xFFFFFFFFu) flush(cur);
+  for (int j = 0; j < len; j += PD) {
 #pragma unroll
-      for (int q = 0; q < KM; ++q) acc[q] = T(0);
-      cur = code;
+    for (int d = 0; d < PD; ++d) {
+      if (j + d < len) {
+        if (cc[d] != cur) {
+          if (cur != 0xFFFFFFFFu) flush(cur);
+#pragma unroll
+          for (int q = 0; q < KM; ++q) acc[q] = T(0);
+          cur = cc[d];
+        }
+#pragma unroll
+        for (int q = 0; q < KM; ++q) acc[q] += xr[d][q];
+      }
+      load_row(d, j + d + PD, nx[d]);
+      nx[d] = index_of(j + d + 2 * PD);
     }
-    const T* xr = X + (int64_t)__ldg(pos_n + __ldg(perm + sl)) * Km;
-#pragma unroll
-    for (int q = 0; q < KM; ++q)
-      if (q < Km) acc[q] += __ldg(xr + q);
   }
-  if (len > 0) flush(cur);
+  flush(cur);
 }
 
 // dF[row_id[r]][k] += Zc[r][k]
@@ -1004,12 +1027,17 @@ void reduce_into(tucker_ctx* c, int m, int n, const T* X, T* dF, cudaStream_t s)
   T* Zc = (T*)c->bwd_Zc;
   T* Zp = (T*)c->bwd_Zp;
   const unsigned grid = (unsigned)tk_ceil_div(md.Pa, 128);
+  // rows in flight per thread: 128 registers' worth
+  constexpr int R = 128 * 4 / (int)sizeof(T);
   if (Km <= 8)
-    k_bwd_reduce<T, 8><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+    k_bwd_reduce<T, 8, R / 8 < 8 ? R / 8 : 8><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len,
+                                                                    md.Pa, md.limit, Zc, Zp);
   else if (Km <= 16)
-    k_bwd_reduce<T, 16><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+    k_bwd_reduce<T, 16, R / 16><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len, md.Pa, md.limit,
+                                                    Zc, Zp);
   else
-    k_bwd_reduce<T, 32><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len, md.Pa, md.limit, Zc, Zp);
+    k_bwd_reduce<T, 32, R / 32><<<grid, 128, 0, s>>>(X, Km, md.perm, pos_n, md.rowcode, md.bin_len, md.Pa, md.limit,
+                                                    Zc, Zp);
   TK_CUDA(cudaGetLastError());
   if (md.nsplit > 0) {
     dim3 g1(md.nchunks, (unsigned)tk_ceil_div(Km, 32));

@@ -73,6 +73,8 @@ SIGNATURES = {
     "tucker_last_error": (ctypes.c_char_p, [_VP]),
     "tucker_stats": (ctypes.c_int, [_VP, ctypes.c_int, _P64, _P64, _P64, _P64, _P64]),
     "tucker_ttm_form": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), _P64]),
+    "tucker_scheme_metrics": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int, _VP, _P64, _P64, _P64,
+                                             _VP, _VP, _VP]),
     "tucker_partition": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "tucker_partition_noalloc": (ctypes.c_int, [_VP, ctypes.c_int, _VP, _VP, _VP]),
     "ttm_chain": (ctypes.c_int, [_VP, ctypes.c_int, ctypes.POINTER(_VP), _VP, _VP, _VP, _VP]),
@@ -226,6 +228,22 @@ class Tucker:
         v = [ctypes.c_int64() for _ in range(5)]
         self._check(self.lib.tucker_stats(self.h, mode, *[ctypes.byref(x) for x in v]))
         return dict(zip(("E_max", "R_sum", "R_max", "R_n", "P"), (x.value for x in v)))
+
+    def scheme_metrics(self, mode, scheme, P, pos):
+        """Section 4.1 metrics of CoarseG (scheme "coarseg") or MediumG ("mediumg")
+        along `mode` for P processors; pos: N int32 CUDA tensors, pos[m][l] =
+        position of index l of mode m in the random order.  Returns E_max,
+        R_sum, R_max and the per-processor E, R (int64 CUDA tensors)."""
+        code = {"coarseg": 1, "mediumg": 2}[scheme]
+        for p in pos:
+            _need_cuda(p, torch.int32, "pos")
+        ptrs = (ctypes.c_void_p * self.N)(*[p.data_ptr() for p in pos])
+        E = torch.empty(P, dtype=torch.int64, device="cuda")
+        R = torch.empty(P, dtype=torch.int64, device="cuda")
+        v = [ctypes.c_int64() for _ in range(3)]
+        self._check(self.lib.tucker_scheme_metrics(self.h, mode, code, int(P), ptrs, *[ctypes.byref(x) for x in v],
+                                                   _ptr(E), _ptr(R), _stream()))
+        return dict(E_max=v[0].value, R_sum=v[1].value, R_max=v[2].value, E=E, R=R)
 
     def ttm_form(self, mode):
         """{"tensor_cores": bool, "blocks": padded 8-element blocks (0 on CUDA cores)}"""
