@@ -13,6 +13,8 @@ beyond chunking the element loop to bound memory:
 * ``kron_row``            -- Appendix A (Kronecker vectorisation, first vector fastest)
 * ``ttm_chain``           -- Section 3, eq. (1): Z_(n)[l,:] = sum_{e in Slice_n^l} val(e) Kron_n(e)
 * ``leading_left_singular_vectors`` -- Section 2.2 / Fig. 1 "SVD" step
+* ``lanczos_bidiagonalization``, ``lanczos_factor`` -- the paper's SVD route
+                            (Section 3 "SVD component", Section 7: 2K iterations)
 * ``hooi_invocation``     -- Fig. 1 (Jacobi reading: every mode uses the input factors)
 * ``core``                -- Fig. 1 "New core": G = T x_1 F_1^T ... x_N F_N^T
 * ``fit``                 -- Kolda-Bader fit via ||T - [[G;F]]||^2 = ||T||^2 - ||G||^2
@@ -107,6 +109,75 @@ def leading_left_singular_vectors(Z, K):
     U = np.zeros((Z.shape[0], K))
     U[nz] = Uc[:, :K]
     return sign_normalise(U), s[:K].copy()
+
+
+def lanczos_bidiagonalization(Z, m, v0):
+    """Golub-Kahan-Lanczos bidiagonalisation of Z (R x Khat), m steps from the
+    start vector v0 -- the matrix-free iteration of Section 3 ("SVD
+    component"), in which every step asks for one product Z x and one product
+    y Z.  Both bases are re-orthogonalised in full (classical Gram-Schmidt,
+    twice).  Returns (U, V, alpha, beta): U is R x m, V is Khat x m, both with
+    orthonormal columns, and Z V = U B with B upper bidiagonal, alpha on its
+    diagonal and beta[:m-1] above it (beta[m-1] is the residual norm of the
+    last step).  Stops early at an invariant subspace (a zero alpha or beta)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    R, kh = Z.shape
+    U = np.zeros((R, m))
+    V = np.zeros((kh, m + 1))
+    alpha = np.zeros(m)
+    beta = np.zeros(m)
+    V[:, 0] = np.asarray(v0, dtype=np.float64) / np.linalg.norm(v0)
+    done = m
+    for j in range(m):
+        p = Z @ V[:, j]
+        if j > 0:
+            p -= beta[j - 1] * U[:, j - 1]
+        for _ in range(2):
+            p -= U[:, :j] @ (U[:, :j].T @ p)
+        alpha[j] = np.linalg.norm(p)
+        if alpha[j] == 0.0:
+            done = j
+            break
+        U[:, j] = p / alpha[j]
+        r = Z.T @ U[:, j] - alpha[j] * V[:, j]
+        for _ in range(2):
+            r -= V[:, : j + 1] @ (V[:, : j + 1].T @ r)
+        beta[j] = np.linalg.norm(r)
+        if beta[j] == 0.0:
+            done = j + 1
+            break
+        V[:, j + 1] = r / beta[j]
+    return U[:, :done], V[:, :done], alpha[:done], beta[:done]
+
+
+def lanczos_factor(Z, K, m=None, v0=None):
+    """F~_n by the paper's SVD route (Section 3 "SVD component"; Section 7: a
+    Lanczos bidiagonalisation with m = 2K iterations).  The K leading singular
+    triplets of the m x m bidiagonal B give the right vectors V_K = V Q_K and
+    sigma_K; then U = Z V_K diag(1/sigma_K), orthonormalised (QR with a positive
+    diagonal) and sign-normalised -- the same back-projection as the exact
+    route.  Readings: v0 = the all-ones vector (the paper's library starts
+    from a random vector; a fixed one keeps both sides on the same Krylov
+    space); m = min(2K, Khat, non-empty rows).  As in
+    ``leading_left_singular_vectors`` the iteration runs over the non-empty
+    rows.  Returns (U, sigma)."""
+    Z = np.asarray(Z, dtype=np.float64)
+    nz = np.flatnonzero(np.any(Z != 0.0, axis=1))
+    Zc = Z[nz]
+    R, kh = Zc.shape
+    m = min(2 * K if m is None else m, kh, R)
+    v0 = np.ones(kh) if v0 is None else v0
+    U, V, alpha, beta = lanczos_bidiagonalization(Zc, m, v0)
+    mm = len(alpha)
+    B = np.diag(alpha) + np.diag(beta[: mm - 1], 1)
+    _, s, Qt = np.linalg.svd(B)
+    VK = V @ Qt[:K].T
+    Uc = Zc @ VK / s[:K]
+    Q, Rr = np.linalg.qr(Uc)
+    Q = Q * np.sign(np.diag(Rr))
+    out = np.zeros((Z.shape[0], K))
+    out[nz] = Q
+    return sign_normalise(out), s[:K].copy()
 
 
 def hooi_invocation(L, idx, vals, F, K=None, variant="jacobi"):
