@@ -332,6 +332,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     tk = Tucker(idx_d, vals_d, L, K, prec=args.prec, timing=True)
     torch.cuda.synchronize()
+    forms = [tk.ttm_form(n)["tensor_cores"] for n in range(N)]
+    ttm_kernel = "k_ttmc_tc" if all(forms) else ("k_ttmc_fwd" if not any(forms) else "k_ttmc_fwd + k_ttmc_tc")
     partition_s = time.perf_counter() - t0
     R = tk.R
     stats = [tk.stats(n) for n in range(N)]
@@ -475,7 +477,7 @@ def run_ours(args):
                         parallelism="replicas" if world > 1 else "single GPU"),
             roofline=dict(bound="hbm", achieved=round(achieved_gbs, 1), peak=pk["hbm_gbs"], unit="GB/s",
                           frac=round(achieved_gbs / pk["hbm_gbs"], 4), traffic=traffic,
-                          kernel="k_ttmc_fwd", peak_source=pk["source"] + " (hbm_gbs)",
+                          kernel=ttm_kernel, peak_source=pk["source"] + " (hbm_gbs)",
                           bytes_per_launch=int(bytes_per_launch), ms_per_launch=round(ttm_s_per_launch * 1e3, 4),
                           alu_tflops=round(achieved_tflops, 2), alu_frac_fp32=round(achieved_tflops / fp32_peak_tflops, 4)),
             ttm_chain_gbs=round(achieved_gbs, 1), ttm_chain_frac_hbm=round(achieved_gbs / pk["hbm_gbs"], 4),

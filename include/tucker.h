@@ -102,7 +102,14 @@ typedef struct {
   tucker_alloc_fn alloc; /* NULL: the library calls cudaMalloc / cudaFree itself          */
   tucker_free_fn free;   /* must be non-NULL exactly when alloc is                        */
   void* alloc_user;      /* passed to alloc and free                                      */
-  int32_t reserved[4];   /* must be zero                                                  */
+  int32_t svd;           /* factor update: 0 = the exact leading subspace of Z (Gram       *
+                          * W = Z^T Z, eigensolve, back-projection); 1 = the paper's      *
+                          * route (Section 3 "SVD component", Section 7): a Lanczos        *
+                          * bidiagonalisation of Z with m = min(2 K_n, Khat_n, R_n) steps  *
+                          * from the all-ones start vector, full re-orthogonalisation,     *
+                          * then the same back-projection (an approximation of the         *
+                          * subspace; it keeps R_n x m FP64 Lanczos vectors per mode)      */
+  int32_t reserved[3];   /* must be zero                                                  */
 } tucker_opts;
 
 /* Fills *opts with the defaults (FP32, automatic P, Jacobi reading, no timing,

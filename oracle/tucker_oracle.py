@@ -180,13 +180,14 @@ def lanczos_factor(Z, K, m=None, v0=None):
     return sign_normalise(out), s[:K].copy()
 
 
-def hooi_invocation(L, idx, vals, F, K=None, variant="jacobi"):
+def hooi_invocation(L, idx, vals, F, K=None, variant="jacobi", svd="exact"):
     """One invocation of the HOOI procedure of Fig. 1 (without the core).
 
     For each mode n: Z <- T x_{m != n} F_m^T (TTM-chain), F~_n <- leading K_n
     left singular vectors of Z_(n).  ``variant="jacobi"`` takes every TTM-chain
     from the input factors (Fig. 1 as printed); ``"gauss_seidel"`` uses the
-    factors already refined in this invocation (textbook HOOI)."""
+    factors already refined in this invocation (textbook HOOI).  ``svd="lanczos"``
+    takes the factor by the paper's Lanczos route (``lanczos_factor``)."""
     N = len(F)
     if K is None:
         K = [np.asarray(f).shape[1] for f in F]
@@ -194,7 +195,10 @@ def hooi_invocation(L, idx, vals, F, K=None, variant="jacobi"):
     for n in range(N):
         src = F if variant == "jacobi" else new
         Z = ttm_chain(L, idx, vals, src, n)
-        new[n], _ = leading_left_singular_vectors(Z, K[n])
+        if svd == "lanczos":
+            new[n], _ = lanczos_factor(Z, K[n])
+        else:
+            new[n], _ = leading_left_singular_vectors(Z, K[n])
     return new
 
 
@@ -230,12 +234,12 @@ def fit(vals, G):
     return 1.0 - np.sqrt(max(0.0, t2 - g2)) / np.sqrt(t2)
 
 
-def hooi(L, idx, vals, F0, iters, variant="jacobi"):
+def hooi(L, idx, vals, F0, iters, variant="jacobi", svd="exact"):
     """``iters`` invocations of Fig. 1 followed by the core, computed once after
     all invocations (Section 2.2).  Returns (F, G, fit)."""
     F = [np.asarray(f, dtype=np.float64) for f in F0]
     for _ in range(iters):
-        F = hooi_invocation(L, idx, vals, F, variant=variant)
+        F = hooi_invocation(L, idx, vals, F, variant=variant, svd=svd)
     G = core(L, idx, vals, F)
     return F, G, fit(vals, G)
 

@@ -221,8 +221,9 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     if (o.P_bins < 0) tk_throw(TUCKER_ERR_ARG, "P_bins must be >= 0");
     if (o.wait_cap < -1) tk_throw(TUCKER_ERR_ARG, "wait_cap must be >= -1");
     if (o.ttm_path != 0 && o.ttm_path != 1) tk_throw(TUCKER_ERR_ARG, "ttm_path must be 0 or 1");
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 3; ++i)
       if (o.reserved[i]) tk_throw(TUCKER_ERR_ARG, "reserved option fields must be zero");
+    if (o.svd != 0 && o.svd != 1) tk_throw(TUCKER_ERR_ARG, "svd must be 0 or 1");
     if ((o.alloc == nullptr) != (o.free == nullptr)) tk_throw(TUCKER_ERR_ARG, "alloc and free must be set together");
     for (int m = 0; m < N; ++m) {
       if (L[m] < 1 || L[m] >= ((int64_t)1 << 31) - 1) tk_throw(TUCKER_ERR_ARG, "mode length out of range");
@@ -238,6 +239,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     c->esz = c->prec == TUCKER_FP32 ? 4 : 8;
     c->gauss_seidel = o.gauss_seidel != 0;
     c->ttm_path = o.ttm_path;
+    c->svd_lanczos = o.svd;
     c->timing = o.timing != 0;
     c->wait_cap = o.wait_cap;
     c->sm_count = tk_sm_count();
@@ -311,6 +313,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
     for (int n = 0; n < N; ++n) {
       c->Zm[n] = tk_alloc(c, (size_t)std::max(c->mode[n].R, 1) * c->mode[n].Khat * esz);
       tk_alloc_fuws(c, n);
+      if (c->svd_lanczos) tk_lanczos_alloc(c, n);
       TK_CUDA(cudaStreamCreateWithFlags(&c->aux[n], cudaStreamNonBlocking));
       TK_CUDA(cudaEventCreateWithFlags(&c->ev_ttm[n], cudaEventDisableTiming));
       TK_CUDA(cudaEventCreateWithFlags(&c->ev_fu[n], cudaEventDisableTiming));

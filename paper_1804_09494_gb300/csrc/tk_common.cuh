@@ -83,6 +83,18 @@ struct tk_buf {
   size_t bytes = 0;
 };
 
+// Scratch of the Lanczos bidiagonalisation route of one mode (tk_lanczos.cu)
+struct tk_lzws {
+  double* U = nullptr;       // R x m, column-major: the left Lanczos vectors
+  double* p = nullptr;       // R
+  double* V = nullptr;       // Khat x (m + 1), column-major: the right Lanczos vectors
+  double* part = nullptr;    // row-block partial sums (blocks x 64)
+  double* part_c = nullptr;  // row-block partials of u^T Z (blocks x Khat)
+  double* cf = nullptr;      // Gram-Schmidt coefficients
+  double* alpha = nullptr;   // diagonal of B
+  double* beta = nullptr;    // superdiagonal of B
+};
+
 // Scratch of one factor update (Gram, eigensolve, back-projection, CholeskyQR2).
 struct tk_fuws {
   void* Wpart = nullptr;    // Gram split partials
@@ -102,6 +114,7 @@ struct tk_fuws {
   double* Cpart = nullptr;  // 4 * SMs x TK_MAXK^2
   double* Rinv = nullptr;   // 3 x TK_MAXK^2
   double* colbest = nullptr;// 2 * SMs x TK_MAXK x 3
+  tk_lzws lz;               // Lanczos route only
 };
 
 struct tucker_ctx {
@@ -114,6 +127,7 @@ struct tucker_ctx {
   size_t esz = 4;
   int gauss_seidel = 0;
   int ttm_path = 0;         // 0: tensor-core TTM-chain where eligible, 1: CUDA cores only
+  int svd_lanczos = 0;      // factor update: 0 exact leading subspace (Gram), 1 Lanczos bidiagonalisation
   int timing = 0;
   int sm_count = 0;
   double normT2 = 0.0;
@@ -254,6 +268,14 @@ void tk_alloc_fuws(tucker_ctx* c, int n);
 // NULL) receive E^p and R^p.  Synchronises s.
 void tk_scheme_metrics(tucker_ctx* c, int n, int scheme, int P, const int32_t* const* d_pos, int64_t* out3,
                        int64_t* d_E, int64_t* d_R, cudaStream_t s);
+
+// ---- the Lanczos route of the factor update (tk_lanczos.cu) ----
+void tk_lanczos_alloc(tucker_ctx* c, int n);
+// runs the bidiagonalisation of Z, writes W = B^T B (m x m) into the mode's
+// factor-update workspace and returns m
+int tk_lanczos_bidiag(tucker_ctx* c, int n, const void* Z, cudaStream_t s);
+// after the eigensolve of B^T B: V (m x K) -> V_K = V_lanczos Q (Khat x K), Vs
+void tk_lanczos_vk(tucker_ctx* c, int n, int m, cudaStream_t s);
 
 // ---- core / fit (tk_core.cu) ----
 // New core from the TTM-chain of mode tk_core_mode(c); with before_Fn, the

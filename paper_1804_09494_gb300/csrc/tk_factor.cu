@@ -1796,9 +1796,15 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
   const T* Z = (const T*)Zv;
   const int sms = c->sm_count;
 
-  // ---- Gram W = Z^T Z
+  // ---- Gram W = Z^T Z (exact route), or the Lanczos bidiagonalisation of Z
+  // with W = B^T B of its m x m bidiagonal (the paper's route)
+  int eig_n = Khat;
   tk_phase_begin(c, PH_GRAM, s);
   bool gram_done = false;
+  if (c->svd_lanczos) {
+    eig_n = tk_lanczos_bidiag(c, n, Z, s);
+    gram_done = true;
+  }
   if constexpr (sizeof(T) == 4) {
     if (!c->gram_bf16 && tk_gram_tc_supported(Khat) && ((uintptr_t)Z % 16 == 0)) {
       // tensor cores: per-CTA partials, reduced and symmetrised in FP64
@@ -1848,16 +1854,16 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     setup_eig_attr<T>();
     EigArgs<T> a{};
     a.W = ws->W;
-    a.n = Khat;
+    a.n = eig_n;
     a.K = K;
     a.gA = (T*)ws->eigA;
     a.gQ = (T*)ws->eigV;
-    const size_t mat = (size_t)2 * Khat * Khat * sizeof(T);
-    const size_t work = (size_t)5 * Khat * sizeof(T) + 64;
+    const size_t mat = (size_t)2 * eig_n * eig_n * sizeof(T);
+    const size_t work = (size_t)5 * eig_n * sizeof(T) + 64;
     a.use_smem = (mat + work) <= 150 * 1024;
     const size_t shm = (a.use_smem ? mat : 0) + work;
-    const size_t shm_small = eig_small_smem<T>(Khat, K);
-    const bool small = Khat <= 2 * kEigSmallThreads && shm_small <= kEigSmallSmemMax;
+    const size_t shm_small = eig_small_smem<T>(eig_n, K);
+    const bool small = eig_n <= 2 * kEigSmallThreads && shm_small <= kEigSmallSmemMax;
     a.polish = c->prec == TUCKER_FP32;
     a.X = ws->eigX;
     a.Y = ws->eigX + (size_t)Khat * K;
@@ -1869,8 +1875,8 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     a.err = c->err;
     bool v4 = false;
     if constexpr (sizeof(T) == 4) {
-      const size_t shm_v4 = eig_v4_smem(Khat, K);
-      if (Khat <= kEigV4MaxN && shm_v4 <= kEigSmallSmemMax) {
+      const size_t shm_v4 = eig_v4_smem(eig_n, K);
+      if (eig_n <= kEigV4MaxN && shm_v4 <= kEigSmallSmemMax) {
         k_eig_v4<<<1, kEigSmallThreads, shm_v4, s>>>(a);
         v4 = true;
       }
@@ -1880,6 +1886,12 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     else k_eig<T><<<1, 1024, shm, s>>>(a);
     TK_CUDA(cudaGetLastError());
     tk_launched(c, PH_EIG);
+    // Lanczos route: the eigenvectors of B^T B are B's right singular vectors Q;
+    // the right singular vectors of Z are V_K = V_lanczos Q_K
+    if (c->svd_lanczos) {
+      tk_lanczos_vk(c, n, eig_n, s);
+      tk_launched(c, PH_EIG);
+    }
   }
   tk_phase_end(c, s);
 

@@ -64,7 +64,7 @@ struct TtmcArgs {
   int KA, KB;
   int Khat;
   int store_vec;
-  int chunk;  // staged steps per buffer
+  int tile_vec;  // adjoint: the cotangent block rows can be read as 16-byte vectors
   T* Z;
   T* Zpart;
   // adjoint
@@ -82,64 +82,13 @@ __device__ __forceinline__ void unpack(const double2& x, double* o) {
   o[0] = x.x;
   o[1] = x.y;
 }
-__device__ __forceinline__ float4 pack(const float* i) { return make_float4(i[0], i[1], i[2], i[3]); }
-__device__ __forceinline__ double2 pack(const double* i) { return make_double2(i[0], i[1]); }
 
 template <typename T, int M>
 struct Row {
   static constexpr int W = VecT<T>::W;
   static constexpr int NV = (M + W - 1) / W;
-  static constexpr int R = NV * W;
 };
 
-// Loads the first `valid` entries of a 16-byte aligned row (whole vectors);
-// entries past `valid` inside a loaded vector are the row's zero padding.
-template <typename T, int M>
-__device__ __forceinline__ void load_row(const T* __restrict__ row, int valid, T (&out)[Row<T, M>::R]) {
-  using V = typename VecT<T>::type;
-  constexpr int W = VecT<T>::W;
-#pragma unroll
-  for (int v = 0; v < Row<T, M>::NV; ++v) {
-    if (v * W < valid) {
-      unpack(__ldg(reinterpret_cast<const V*>(row) + v), &out[v * W]);
-    } else {
-#pragma unroll
-      for (int u = 0; u < W; ++u) out[v * W + u] = T(0);
-    }
-  }
-}
-
-// The same through the texture path (texel = one 16-byte vector), so that the
-// two gathered rows of an element use the LSU and the texture pipelines.
-__device__ __forceinline__ void tex_vec(cudaTextureObject_t t, int i, float* o) {
-  unpack(tex1Dfetch<float4>(t, i), o);
-}
-__device__ __forceinline__ void tex_vec(cudaTextureObject_t t, int i, double* o) {
-  const int4 v = tex1Dfetch<int4>(t, i);
-  o[0] = __hiloint2double(v.y, v.x);
-  o[1] = __hiloint2double(v.w, v.z);
-}
-template <typename T, int M>
-__device__ __forceinline__ void tex_row(cudaTextureObject_t t, int64_t first, int valid, T (&out)[Row<T, M>::R]) {
-  constexpr int W = VecT<T>::W;
-#pragma unroll
-  for (int v = 0; v < Row<T, M>::NV; ++v) {
-    if (v * W < valid) {
-      tex_vec(t, (int)(first / W) + v, &out[v * W]);
-    } else {
-#pragma unroll
-      for (int u = 0; u < W; ++u) out[v * W + u] = T(0);
-    }
-  }
-}
-
-// Loads issued in program order (volatile), so that the rows of two elements
-// are all requested before either is used.
-__device__ __forceinline__ float4 ldg_v4_ordered(const float* p) {
-  float4 v;
-  asm volatile("ld.global.nc.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p));
-  return v;
-}
 __device__ __forceinline__ float4 tex_v4_ordered(cudaTextureObject_t t, int i) {
   float4 v;
   asm volatile("tex.1d.v4.f32.s32 {%0, %1, %2, %3}, [%4, {%5}];"
@@ -148,11 +97,6 @@ __device__ __forceinline__ float4 tex_v4_ordered(cudaTextureObject_t t, int i) {
   return v;
 }
 
-// ---------------------------------------------------------------- staging
-// Each warp streams the element arrays of its 32 bins through shared memory:
-// steps [k0, k0+C) of a warp occupy one contiguous span per array (the
-// warp-interleaved layout), copied with 16-byte cp.async into one of two
-// buffers while the other buffer is being consumed.
 // The element stream and the Z rows are touched once per launch: they are
 // marked evict-first in L2 so that they do not displace the factor rows, which
 // are gathered again and again.
@@ -239,55 +183,6 @@ __device__ __forceinline__ void st_clear1(float* p, float& x, int on) {
 __device__ __forceinline__ void st_clear1(double* p, double& x, int on) {
   asm volatile("{\n .reg .pred q;\n setp.ne.s32 q, %2, 0;\n @q st.global.f64 [%1], %0;\n mov.b64 %0, 0;\n}"
                : "+d"(x) : "l"(p), "r"(on) : "memory");
-}
-
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(sa), "l"(gsrc),
-               "l"(l2_evict_first())
-               : "memory");
-}
-__device__ __forceinline__ void st_stream(float4* p, const float4& v) {
-  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
-               "f"(v.w), "l"(l2_evict_first())
-               : "memory");
-}
-__device__ __forceinline__ void st_stream(double2* p, const double2& v) {
-  asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;" ::"l"(p), "d"(v.x), "d"(v.y),
-               "l"(l2_evict_first())
-               : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait_0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ void stage_span(void* sdst, const void* gsrc, int bytes, int lane) {
-#pragma unroll 1
-  for (int off = lane * 16; off < bytes; off += 32 * 16) cp_async16((char*)sdst + off, (const char*)gsrc + off);
-}
-
-// One staging buffer of C steps: code[C*32], oidx_q[C*32] (q < nother),
-// then val[C*32] (type T, if staged) and perm[C*32] (if staged).
-template <typename T>
-__host__ __device__ inline int stage_bytes(int C, int nother, bool val, bool perm) {
-  return C * 32 * (4 * (1 + nother) + (val ? (int)sizeof(T) : 0) + (perm ? 4 : 0));
-}
-
-template <typename T>
-__device__ __forceinline__ void issue_chunk(const TtmcArgs<T>& a, char* buf, int CW, int64_t wbase, int k0, int ns,
-                                            int lane, bool val, bool perm) {
-  const int64_t off = (wbase + k0) * 32;
-  const int b4 = ns * 32 * 4;
-  uint32_t* w = (uint32_t*)buf;
-  stage_span(w, a.rowcode + off, b4, lane);
-#pragma unroll 1
-  for (int q = 0; q < a.nother; ++q) stage_span(w + (1 + q) * CW, a.oidx[q] + off, b4, lane);
-  char* vb = (char*)(w + (1 + a.nother) * CW);
-  if (val) {
-    stage_span(vb, a.val + off, ns * 32 * (int)sizeof(T), lane);
-    vb += (size_t)CW * sizeof(T);
-  }
-  if (perm) stage_span(vb, a.perm + off, b4, lane);
 }
 
 constexpr uint32_t kNoCode = 0xFFFFFFFFu;  // no slice yet (row codes stay below 2^31 + 2^30 + 2^30)
@@ -487,10 +382,12 @@ struct BwdOut {
 // Every slot is written by exactly one thread per launch, the 32 threads of a
 // warp write consecutive slots (coalesced rows), there are no atomics and the
 // order of the sums is fixed; the reduction to dF_m gathers X by slot.
-template <typename T, int MA, int MB, bool EA, bool EB>
-__global__ void __launch_bounds__(128) k_bwd_elem(const TtmcArgs<T> a, int g, const BwdOut<T> out) {
-  extern __shared__ __align__(16) char smem[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+template <typename T, int MA, int MB, bool EA, bool EB, int D, bool OUTER, bool OVR>
+__global__ void __launch_bounds__(128, 1) k_bwd_elem(const TtmcArgs<T> a, int g, const BwdOut<T> out) {
+  constexpr int W = VecT<T>::W;
+  constexpr int NA = Row<T, MA>::NV, NB = Row<T, MB>::NV;
+  constexpr int NQ = OUTER ? TK_MAXN - 3 : 1;
+  const int lane = threadIdx.x & 31;
   const int64_t bw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (bw * 32 >= a.P) return;
   const int bin = (int)(bw * 32 + lane);
@@ -500,116 +397,185 @@ __global__ void __launch_bounds__(128) k_bwd_elem(const TtmcArgs<T> a, int g, co
   const int jb = g % a.NB, o = g / a.NB;
   const int j0 = jb * a.TB;
   const int tb = EB ? MB : min(a.TB, a.KB - j0);
-  int oc[TK_MAXN - 3];
-  {
+  const int nq_rt = a.nother - 2;
+  int oc[NQ];
+  if (OUTER) {
     int t = o;
-    for (int q = 2; q < a.nother; ++q) {
-      oc[q - 2] = t % a.Kf[q];
-      t /= a.Kf[q];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      oc[q] = q < nq_rt ? t % a.Kf[q + 2] : 0;
+      if (q < nq_rt) t /= a.Kf[q + 2];
     }
   }
   const int colbase = a.KA * j0 + a.KA * a.KB * o;
-  const int64_t wbase = bw * a.limit;
-  const int C = a.chunk;
-  const bool sval = a.vals_override == nullptr;
-  const int sb = stage_bytes<T>(C, a.nother, sval, true);
-  const int CW = C * 32;
-  char* wsm = smem + (size_t)wib * 2 * sb;
+  const int64_t base = bw * a.limit * 32 + lane;  // slot of element k: base + 32 k
+  const uint64_t pf = l2_evict_first(), pl = l2_evict_last();
+  const bool twob = a.nother >= 2;
 
-  T D[MA * MB];
-  uint32_t cur = 0xFFFFFFFFu;
-  const int nch = (wlen + C - 1) / C;
-  if (nch > 0) issue_chunk(a, wsm, CW, wbase, 0, min(C, wlen), lane, sval, true);
-  cp_commit();
-  if (nch > 1) issue_chunk(a, wsm + sb, CW, wbase, C, min(C, wlen - C), lane, sval, true);
-  cp_commit();
-  for (int c = 0; c < nch; ++c) {
-    cp_wait_1();
-    __syncwarp();
-    const uint32_t* sw = (const uint32_t*)(wsm + (c & 1) * sb);
-    const T* sv = (const T*)(sw + (1 + a.nother) * CW);
-    const int32_t* sp = (const int32_t*)((const char*)sv + (sval ? (size_t)CW * sizeof(T) : 0));
-    const int ns = min(C, wlen - c * C);
-#pragma unroll 1
-    for (int j = 0; j < ns; ++j) {
-      if (c * C + j >= len) break;
-      const int sj = j * 32 + lane;
-      const uint32_t code = sw[sj];
-      if (code != cur) {
-        const T* src = a.dZ + (int64_t)(code & TK_ROW_MASK) * a.Khat + colbase;
+  T Dt[MA * MB];  // the cotangent block of the current slice
+  uint32_t cur = kNoCode;
+
+  // the element pipeline of the forward kernel: coordinates 2D ahead, rows D
+  // ahead, padding slots valid (zeroed at init)
+  int nla[D], nlb[D], nq[D][NQ];
+  auto slot = [&](int k) __attribute__((always_inline)) { return base + (int64_t)min(k, a.limit - 1) * 32; };
+  auto fetch = [&](int d, int k) __attribute__((always_inline)) {
+    const int64_t sl = slot(k);
+    nla[d] = ld_stream(a.oidx[0] + sl, pf);
+    nlb[d] = twob ? ld_stream(a.oidx[1] + sl, pf) : 0;
+    if (OUTER) {
 #pragma unroll
-        for (int jj = 0; jj < MB; ++jj)
+      for (int q = 0; q < NQ; ++q) nq[d][q] = q < nq_rt ? ld_stream(a.oidx[q + 2] + sl, pf) : 0;
+    }
+  };
+  constexpr int RA = (EA && sizeof(T) == 4 && MA % 4 == 2) ? MA : NA * W;
+  constexpr int RB = (EB && sizeof(T) == 4 && MB % 4 == 2) ? MB : NB * W;
+  T A[D][RA], B[D][RB];
+  T v[D], fq[D][NQ];
+  uint32_t code[D];
+  auto issue = [&](int d, int k) __attribute__((always_inline)) {
+    {
+      const int64_t sl = slot(k);
+      code[d] = ld_stream(a.rowcode + sl, pf);
+      if (OVR) v[d] = __ldg(a.vals_override + ld_stream(a.perm + sl, pf));
+      else v[d] = ld_stream(a.val + sl, pf);
+    }
+    const T* ra = a.F[0] + (int64_t)nla[d] * a.ld[0];
 #pragma unroll
-          for (int i = 0; i < MA; ++i)
-            D[i + MA * jj] = ((EB || jj < tb) && (EA || i < ka)) ? __ldg(src + i + a.KA * jj) : T(0);
-        cur = code;
-      }
-      const int32_t e = sp[sj];
-      const T w = sval ? sv[sj] : a.vals_override[e];
-      T fq[TK_MAXN - 3];
-      T so = T(1);
-      for (int q = 2; q < a.nother; ++q) {
-        fq[q - 2] = __ldg(a.F[q] + (int64_t)(int32_t)sw[(1 + q) * CW + sj] * a.ld[q] + oc[q - 2]);
-        so *= fq[q - 2];
-      }
-      T fa[Row<T, MA>::R];
-      load_row<T, MA>(a.F[0] + (int64_t)(int32_t)sw[CW + sj] * a.ld[0], ka, fa);
-      T fb[Row<T, MB>::R];
-      if (a.nother >= 2) {
-        load_row<T, MB>(a.F[1] + (int64_t)(int32_t)sw[2 * CW + sj] * a.ld[1] + j0, tb, fb);
-      } else {
-#pragma unroll
-        for (int u = 0; u < Row<T, MB>::R; ++u) fb[u] = T(u == 0);
-      }
-      T x[MA], y[MB];
-#pragma unroll
-      for (int i = 0; i < MA; ++i) x[i] = T(0);
-#pragma unroll
-      for (int jj = 0; jj < MB; ++jj) {
-        T yy = T(0);
-#pragma unroll
-        for (int i = 0; i < MA; ++i) {
-          x[i] = fma(D[i + MA * jj], fb[jj], x[i]);
-          yy = fma(D[i + MA * jj], fa[i], yy);
-        }
-        y[jj] = yy;
-      }
-      T dot = T(0);
-#pragma unroll
-      for (int i = 0; i < MA; ++i) dot = fma(fa[i], x[i], dot);
-      const int64_t slot = (wbase + (int64_t)c * C + j) * 32 + lane;
-      if (out.dv) {
-        T* dv = out.dv + slot;
-        *dv = out.first_dv ? so * dot : *dv + so * dot;
-      }
-      const T ws = w * so;
-      if (out.X[0]) {
-        T* xr = out.X[0] + slot * a.KA;
-        const bool f = out.first[0] != 0;
-#pragma unroll
-        for (int i = 0; i < MA; ++i)
-          if (EA || i < ka) xr[i] = f ? ws * x[i] : xr[i] + ws * x[i];
-      }
-      if (a.nother >= 2 && out.X[1]) {
-        T* xr = out.X[1] + slot * a.KB + j0;
-        const bool f = out.first[1] != 0;
-#pragma unroll
-        for (int jj = 0; jj < MB; ++jj)
-          if (EB || jj < tb) xr[jj] = f ? ws * y[jj] : xr[jj] + ws * y[jj];
-      }
-      for (int q = 2; q < a.nother; ++q) {
-        if (!out.X[q]) continue;
-        T prod = w * dot;
-        for (int q2 = 2; q2 < a.nother; ++q2)
-          if (q2 != q) prod *= fq[q2 - 2];
-        out.X[q][slot * a.Kf[q] + oc[q - 2]] += prod;
+    for (int u = 0; u < NA; ++u) {
+      if (u * W + W <= RA) {
+        if (EA || u * W < ka) unpack(ld_row(ra + u * W, pl), &A[d][u * W]);
+        else for (int w = 0; w < W; ++w) A[d][u * W + w] = T(0);
+      } else if constexpr (sizeof(T) == 4) {
+        const float2 t = ld_row2((const float*)ra + u * W, pl);
+        A[d][u * W] = t.x;
+        A[d][u * W + 1] = t.y;
       }
     }
-    __syncwarp();
-    if (c + 2 < nch) issue_chunk(a, wsm + (c & 1) * sb, CW, wbase, (c + 2) * C, min(C, wlen - (c + 2) * C), lane, sval, true);
-    cp_commit();
+    if (twob) {
+      const T* rb = a.F[1] + (int64_t)nlb[d] * a.ld[1] + j0;
+#pragma unroll
+      for (int u = 0; u < NB; ++u) {
+        if (u * W + W <= RB) {
+          if (EB || u * W < tb) unpack(ld_row(rb + u * W, pl), &B[d][u * W]);
+          else for (int w = 0; w < W; ++w) B[d][u * W + w] = T(0);
+        } else if constexpr (sizeof(T) == 4) {
+          const float2 t = ld_row2((const float*)rb + u * W, pl);
+          B[d][u * W] = t.x;
+          B[d][u * W + 1] = t.y;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < RB; ++u) B[d][u] = T(u == 0);
+    }
+    if (OUTER) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        fq[d][q] = q < nq_rt ? __ldg(a.F[q + 2] + (int64_t)nq[d][q] * a.ld[q + 2] + oc[q]) : T(1);
+    }
+  };
+
+#pragma unroll
+  for (int d = 0; d < D; ++d) fetch(d, d);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    issue(d, d);
+    fetch(d, d + D);
   }
-  cp_wait_0();
+#pragma unroll 1
+  for (int j = 0; j < wlen; j += D) {
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+      const int k = j + d;
+      if (k < len) {
+        const uint32_t cd = code[d];
+        if (cd != cur) {
+          const T* src = a.dZ + (int64_t)(cd & TK_ROW_MASK) * a.Khat + colbase;
+          bool done = false;
+          if constexpr (EA && MA % W == 0) {
+            if (a.tile_vec) {
+              using V = typename VecT<T>::type;
+#pragma unroll
+              for (int jj = 0; jj < MB; ++jj) {
+#pragma unroll
+                for (int u = 0; u < MA / W; ++u) {
+                  if (EB || jj < tb) unpack(__ldg(reinterpret_cast<const V*>(src + a.KA * jj) + u), &Dt[MA * jj + u * W]);
+                  else
+#pragma unroll
+                    for (int w = 0; w < W; ++w) Dt[MA * jj + u * W + w] = T(0);
+                }
+              }
+              done = true;
+            }
+          }
+          if (!done) {
+#pragma unroll
+            for (int jj = 0; jj < MB; ++jj)
+#pragma unroll
+              for (int i = 0; i < MA; ++i)
+                Dt[i + MA * jj] = ((EB || jj < tb) && (EA || i < ka)) ? __ldg(src + i + a.KA * jj) : T(0);
+          }
+          cur = cd;
+        }
+        T so = T(1);
+        if (OUTER) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) so *= fq[d][q];
+        }
+        T x[MA], y[MB];
+#pragma unroll
+        for (int i = 0; i < MA; ++i) x[i] = T(0);
+#pragma unroll
+        for (int jj = 0; jj < MB; ++jj) {
+          T yy = T(0);
+#pragma unroll
+          for (int i = 0; i < MA; ++i) {
+            x[i] = fma(Dt[i + MA * jj], B[d][jj], x[i]);
+            yy = fma(Dt[i + MA * jj], A[d][i], yy);
+          }
+          y[jj] = yy;
+        }
+        T dot = T(0);
+#pragma unroll
+        for (int i = 0; i < MA; ++i) dot = fma(A[d][i], x[i], dot);
+        const int64_t sl = base + (int64_t)k * 32;
+        if (out.dv) {
+          T* dv = out.dv + sl;
+          *dv = out.first_dv ? so * dot : *dv + so * dot;
+        }
+        const T w = v[d];
+        const T ws = w * so;
+        if (out.X[0]) {
+          T* xr = out.X[0] + sl * a.KA;
+          const bool f = out.first[0] != 0;
+#pragma unroll
+          for (int i = 0; i < MA; ++i)
+            if (EA || i < ka) xr[i] = f ? ws * x[i] : xr[i] + ws * x[i];
+        }
+        if (twob && out.X[1]) {
+          T* xr = out.X[1] + sl * a.KB + j0;
+          const bool f = out.first[1] != 0;
+#pragma unroll
+          for (int jj = 0; jj < MB; ++jj)
+            if (EB || jj < tb) xr[jj] = f ? ws * y[jj] : xr[jj] + ws * y[jj];
+        }
+        if (OUTER) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) {
+            if (q >= nq_rt || !out.X[q + 2]) continue;
+            T prod = w * dot;
+#pragma unroll
+            for (int q2 = 0; q2 < NQ; ++q2)
+              if (q2 != q && q2 < nq_rt) prod *= fq[d][q2];
+            out.X[q + 2][sl * a.Kf[q + 2] + oc[q]] += prod;
+          }
+        }
+      }
+      issue(d, j + d + D);
+      fetch(d, j + d + 2 * D);
+    }
+  }
 }
 
 // Adjoint, reduction over mode m's copy: every slice of mode m sums the
@@ -649,14 +615,14 @@ __global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int
   T xr[PD][KM];
   uint32_t cc[PD];
   int nx[PD];
-  auto load_row = [&](int d, int k, int p) __attribute__((always_inline)) {
+  auto fetch_row = [&](int d, int k, int p) __attribute__((always_inline)) {
     cc[d] = __ldg(rowcode + slot(k));
     const T* r = X + (int64_t)p * Km;
 #pragma unroll
     for (int q = 0; q < KM; ++q) xr[d][q] = q < Km ? __ldg(r + q) : T(0);
   };
 #pragma unroll
-  for (int d = 0; d < PD; ++d) load_row(d, d, index_of(d));
+  for (int d = 0; d < PD; ++d) fetch_row(d, d, index_of(d));
 #pragma unroll
   for (int d = 0; d < PD; ++d) nx[d] = index_of(d + PD);
 #pragma unroll 1
@@ -673,7 +639,7 @@ __global__ void __launch_bounds__(128) k_bwd_reduce(const T* __restrict__ X, int
 #pragma unroll
         for (int q = 0; q < KM; ++q) acc[q] += xr[d][q];
       }
-      load_row(d, j + d + PD, nx[d]);
+      fetch_row(d, j + d + PD, nx[d]);
       nx[d] = index_of(j + d + 2 * PD);
     }
   }
@@ -826,28 +792,34 @@ KernelT<double> fwd_kernel<double>(int id, bool outer, bool ovr) {
 #undef TK_FWD_PICK
 template <typename T>
 using BwdKernelT = void (*)(TtmcArgs<T>, int, BwdOut<T>);
+// rows in flight per thread for the adjoint: the cotangent block plus D
+// elements' rows within the register budget
+#define TK_BWD_PICK(T, MA, MB, EA, EB, D)                                                                \
+  (outer ? (ovr ? k_bwd_elem<T, MA, MB, EA, EB, D, true, true> : k_bwd_elem<T, MA, MB, EA, EB, D, true, false>) \
+         : (ovr ? k_bwd_elem<T, MA, MB, EA, EB, D, false, true> : k_bwd_elem<T, MA, MB, EA, EB, D, false, false>))
 template <typename T>
-BwdKernelT<T> bwd_kernel(int id);
+BwdKernelT<T> bwd_kernel(int id, bool outer, bool ovr);
 template <>
-BwdKernelT<float> bwd_kernel<float>(int id) {
+BwdKernelT<float> bwd_kernel<float>(int id, bool outer, bool ovr) {
   switch (id) {
-    case 0: return k_bwd_elem<float, 10, 10, true, true>;
-    case 1: return k_bwd_elem<float, 8, 8, true, true>;
-    case 2: return k_bwd_elem<float, 16, 8, true, true>;
-    case 3: return k_bwd_elem<float, 16, 8, false, false>;
-    default: return k_bwd_elem<float, 32, 4, false, false>;
+    case 0: return TK_BWD_PICK(float, 10, 10, true, true, 3);
+    case 1: return TK_BWD_PICK(float, 8, 8, true, true, 4);
+    case 2: return TK_BWD_PICK(float, 16, 8, true, true, 2);
+    case 3: return TK_BWD_PICK(float, 16, 8, false, false, 2);
+    default: return TK_BWD_PICK(float, 32, 4, false, false, 1);
   }
 }
 template <>
-BwdKernelT<double> bwd_kernel<double>(int id) {
+BwdKernelT<double> bwd_kernel<double>(int id, bool outer, bool ovr) {
   switch (id) {
-    case 0: return k_bwd_elem<double, 10, 4, true, false>;
-    case 1: return k_bwd_elem<double, 8, 4, true, true>;
-    case 2: return k_bwd_elem<double, 16, 4, true, true>;
-    case 3: return k_bwd_elem<double, 16, 4, false, false>;
-    default: return k_bwd_elem<double, 32, 2, false, false>;
+    case 0: return TK_BWD_PICK(double, 10, 4, true, false, 2);
+    case 1: return TK_BWD_PICK(double, 8, 4, true, true, 2);
+    case 2: return TK_BWD_PICK(double, 16, 4, true, true, 1);
+    case 3: return TK_BWD_PICK(double, 16, 4, false, false, 1);
+    default: return TK_BWD_PICK(double, 32, 2, false, false, 1);
   }
 }
+#undef TK_BWD_PICK
 
 struct Plan {
   int tile_id;
@@ -911,17 +883,6 @@ TtmcArgs<T> make_args(tucker_ctx* c, int n, const Plan& pl, void* const* F, cons
   return a;
 }
 
-// Staged steps per buffer: 16 for 3-mode FP32, 8 otherwise (keeps a CTA of
-// 4 warps, double-buffered, within 64 KB of shared memory).
-template <typename T>
-int stage_chunk(int nother) {
-  return (sizeof(T) == 4 && nother <= 2) ? 16 : 8;
-}
-
-template <typename K>
-void set_smem_attr(K kernel, int bytes) {
-  TK_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(bytes, 48 * 1024)));
-}
 
 unsigned blocks_for(const tk_mode& md, int G) {
   const int64_t warps = (int64_t)(md.Pa / 32) * G;
@@ -1062,10 +1023,11 @@ void backward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const v
   const Plan pl = make_plan(c, n);
   TtmcArgs<T> a = make_args<T>(c, n, pl, F, ldF, vals_override);
   a.dZ = (const T*)dZ;
-  a.chunk = stage_chunk<T>(pl.nother);
-  const int shm = 4 * 2 * stage_bytes<T>(a.chunk, pl.nother, vals_override == nullptr, true);
-  BwdKernelT<T> kern = bwd_kernel<T>(pl.tile_id);
-  set_smem_attr(kern, shm);
+  {
+    const int W = 16 / (int)sizeof(T);
+    a.tile_vec = ((uintptr_t)dZ % 16 == 0) && md.Khat % W == 0 && pl.KA % W == 0;
+  }
+  BwdKernelT<T> kern = bwd_kernel<T>(pl.tile_id, pl.nother > 2, vals_override != nullptr);
   const unsigned grid = blocks_for(md, 1);
   tk_phase_begin(c, PH_BWD, s);
   ensure_bwd_workspace(c, s);
@@ -1080,7 +1042,7 @@ void backward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const v
       o.first_dv = g == 0;
       o.first[0] = g == 0;
       o.first[1] = g < pl.NB;
-      kern<<<grid, 128, shm, s>>>(a, g, o);
+      kern<<<grid, 128, 0, s>>>(a, g, o);
       TK_CUDA(cudaGetLastError());
     }
     tk_launched(c, PH_BWD, pl.G);

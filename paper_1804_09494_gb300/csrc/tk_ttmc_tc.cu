@@ -26,21 +26,26 @@
 //
 // One CTA takes a contiguous range of bins (balanced by blocks) and streams
 // it in chunks of 32 elements (4 blocks) through a ring of shared-memory
-// stages:
+// stages, with three roles:
 //   * warps 4-7 load: per chunk, warp 4 the values and F_a rows (as val F_a,
 //     transposed), warp 5 the F_b rows, warp 6 the F_c rows as the TF32
 //     hi / lo B operands (K-major, 128-byte swizzle), warp 7 the block table;
-//     the loads of a group of 4 chunks are all in flight before any is stored;
+//     the loads of a group of chunks are all in flight before any is stored;
 //   * warps 0-3 (thread t = tensor-memory lane t = row t of A) form the
-//     chunk's A operand x_e[t] for its 32 elements, split it, and store hi and
-//     lo into tensor memory (tcgen05.st; two buffers);
-//   * thread 0 issues the chunk's MMAs into the accumulator slot of each
-//     block's segment (8 slots of N columns, round robin); the last block of
-//     a segment commits to the slot's mbarrier;
-//   * warps 0-3 read each finished accumulator back (tcgen05.ld) one chunk
-//     later, add it to the segment's running sum, and at the segment's end
-//     store its row of Z (or the split piece's partial, added by the fix-up
-//     in bin order, as for the CUDA-core kernel).
+//     chunk's A operand x_e[t] for its 32 elements, split it, store hi and lo
+//     into tensor memory (tcgen05.st; two buffers) and hand the buffer over;
+//     one chunk later they read each finished accumulator back (tcgen05.ld),
+//     add it to the segment's running sum, and at the segment's end store its
+//     row of Z (or the split piece's partial, added by the fix-up in bin
+//     order, as for the CUDA-core kernel), then release the slot;
+//   * warp 8 issues the MMAs: per block, the accumulator slot of its piece (8
+//     slots of N columns, round robin, a slot reused only once it has been
+//     read back) and three MMAs; where a piece ends, a commit to the slot's
+//     mbarrier.
+// A tcgen05.mma of this shape (M = 128, N = 16, K = 8) occupies its issuing
+// thread for far longer than the tensor core computes it, so the issuer sets
+// the pace: two CTAs share an SM (256 tensor-memory columns each) to run two
+// issuers side by side.
 // Every mbarrier wait is bounded (clock and the context's poll cap); a
 // timeout sets TK_DEV_ERR_TIMEOUT, every role leaves its loop, the CTA waits
 // (bounded) for its MMAs in flight and releases its tensor memory.
@@ -53,7 +58,7 @@ namespace {
 
 using namespace tk_tc;
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 288;  // warps 0-3 build and drain, 4-7 load, 8 issues the MMAs
 constexpr int kChunk = 32;       // elements per stage: 4 blocks of 8
 constexpr int kStages = 8;
 constexpr int kNacc = 8;         // accumulator slots
@@ -166,8 +171,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
   uint64_t* full = (uint64_t*)(sm + kStages * a.stage_bytes);
   uint64_t* empty = full + kStages;
   uint64_t* abar = empty + kStages;  // 2: A buffer free (MMAs of its chunk done)
-  uint64_t* accf = abar + 2;         // kNacc: segment in the slot complete
-  uint64_t* fin = accf + kNacc;
+  uint64_t* afull = abar + 2;        // 2: A buffer written (4 builder warps)
+  uint64_t* accf = afull + 2;        // kNacc: accumulator of the slot complete
+  uint64_t* acce = accf + kNacc;     // kNacc: slot read back (4 builder warps)
+  uint64_t* fin = acce + kNacc;
   uint32_t* tslot = (uint32_t*)(fin + 1);
   float* run = (float*)(fin + 2);    // NP x 128: running sums of the open segment, [n][lane]
   __shared__ int s_fail;
@@ -187,8 +194,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(128));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
     }
-    for (int i = 0; i < 2 + kNacc + 1; ++i)
+    for (int i = 0; i < 2; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&abar[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[i])), "r"(4));
+    }
+    for (int i = 0; i < kNacc; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[i])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[i])), "r"(4));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(fin)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
     const int64_t t0 = a.nblk * blockIdx.x / gridDim.x, t1 = a.nblk * (blockIdx.x + 1) / gridDim.x;
     s_range[0] = a.blk_ptr[lower_bound_i64(a.blk_ptr, a.Pa, t0)];
@@ -209,7 +223,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
   const int64_t e0 = 8 * B0, e1 = 8 * B1;
   volatile int* fail = &s_fail;
 
-  if (warp >= 4) {
+  if (warp >= 4 && warp < 8) {
     // ------------------------------------------------------------ loaders
     const int q = warp - 4;
     const uint64_t pol = policy_evict_first();
@@ -327,14 +341,72 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
       code_c = code_n;
       flag_c = flag_n;
     }
+  } else if (warp == 8) {
+    // ------------------------------------------------------------ MMA issuer
+    // Per chunk, once the builders have written its A: the slot of each
+    // block's accumulator (a new one where a piece starts, after the builders
+    // have read back its previous piece), three MMAs per block, a commit to
+    // the slot's barrier where a piece ends, then the stage and the A buffer
+    // are released by commits.
+    const uint32_t idesc = idesc_tf32(NP);
+    const uint32_t dcol0 = 128;
+    int segc = 0, cur_slot = 0;
+    uint32_t used = 0, epar = 0;
+    for (int c = 0; c < nchunks; ++c) {
+      const int s = c % kStages;
+      unsigned char* st = sm + s * a.stage_bytes;
+      bool ok = wait_warp(&afull[c & 1], (uint32_t)((c >> 1) & 1), a.cap, fail);
+      if (ok) {
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t* info = (const uint32_t*)(st + a.off_info);
+        const int nvb = (int)min((int64_t)4, B1 - B0 - 4 * (int64_t)c);
+        const uint32_t acol = (uint32_t)((c & 1) * 64);
+        const uint64_t dh = sdesc_sw128(smem_u32(st));
+        const uint64_t dl = sdesc_sw128(smem_u32(st + NP * 128));
+        for (int kb = 0; kb < nvb; ++kb) {
+          const uint32_t fl = info[4 + kb];
+          if (fl & kStart) {
+            cur_slot = segc % kNacc;
+            ++segc;
+            if (used & (1u << cur_slot)) {
+              if (!wait_warp(&acce[cur_slot], (epar >> cur_slot) & 1u, a.cap, fail)) {
+                ok = false;
+                break;
+              }
+              epar ^= 1u << cur_slot;
+            }
+            used |= 1u << cur_slot;
+          }
+          if (lane == 0) {
+            const uint32_t d = tmem + dcol0 + (uint32_t)(cur_slot * NP);
+            const uint32_t ah = tmem + acol + 8 * kb, al = ah + 32;
+            const uint64_t k = (uint64_t)(2 * kb);  // +32 bytes per K-step of 8
+            const uint32_t en = (fl & kStart) ? 0u : 1u;
+            mma_tf32_ts(d, ah, dh + k, idesc, en);
+            mma_tf32_ts(d, ah, dl + k, idesc, 1u);
+            mma_tf32_ts(d, al, dh + k, idesc, 1u);
+            if (fl & kEnd) mma_commit(&accf[cur_slot]);
+          }
+          __syncwarp();
+        }
+        if (ok && lane == 0) {
+          mma_commit(&empty[s]);
+          mma_commit(&abar[c & 1]);
+        }
+        __syncwarp();
+      }
+      if (!ok) {
+        atomicOr((int*)&s_fail, 1);
+        break;
+      }
+    }
   } else {
-    // ------------------------------------------------- A operand, MMA, drain
+    // ------------------------------------------------------- A operand, drain
     const int m = tid;  // tensor-memory lane = row of A
     const bool act = m < a.Mu;
     const int ii = act ? m % a.K[0] : 0, jj = act ? m / a.K[0] : 0;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);
     const uint32_t dcol0 = 128;
-    const uint32_t idesc = idesc_tf32(NP);
     uint32_t accpar = 0;
     int segc = 0, cur_slot = 0;
     int npend = 0;
@@ -342,6 +414,9 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
     uint32_t pend_code[4];
     int pend_slot[4];
     bool pend_final[4];
+    // reads back the pieces that ended in the previous chunk (in order), adds
+    // each to the segment's running sum, stores the row at the segment's end,
+    // and releases the slot to the issuer
     auto drain = [&]() -> bool {
       for (int p = 0; p < npend; ++p) {
         const int sl = pend_slot[p];
@@ -359,15 +434,18 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
             for (int t = 0; t < 16; ++t) {
               const int nn = n0 + t;
               if (nn < a.Nu) {
-                float v = __uint_as_float(r[t]);
-                if (has_run) v += run[nn * 128 + m];
-                if (fin_p) dst[m + (int64_t)a.Mu * nn] = v;
-                else run[nn * 128 + m] = v;
+                float x = __uint_as_float(r[t]);
+                if (has_run) x += run[nn * 128 + m];
+                if (fin_p) dst[m + (int64_t)a.Mu * nn] = x;
+                else run[nn * 128 + m] = x;
               }
             }
           }
         }
         has_run = !fin_p;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[sl])) : "memory");
       }
       npend = 0;
       return true;
@@ -377,9 +455,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
       unsigned char* st = sm + s * a.stage_bytes;
       bool ok = wait_warp(&full[s], (uint32_t)((c / kStages) & 1), a.cap, fail);
       if (ok && c >= 2) ok = wait_warp(&abar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), a.cap, fail);
+      if (!ok) {
+        atomicOr((int*)&s_fail, 1);
+        break;
+      }
       uint32_t cds[4], fls[4];
       const int nvb = (int)min((int64_t)4, B1 - B0 - 4 * (int64_t)c);
-      if (ok) {
+      {
         const uint32_t* info = (const uint32_t*)(st + a.off_info);
 #pragma unroll
         for (int kb = 0; kb < 4; ++kb) {
@@ -405,30 +487,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
         tmem_st32(lane_base + acol, h);
         tmem_st32(lane_base + acol + 32, l);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        // the segments that ended in the previous chunk are complete by now
-        if (!drain()) ok = false;
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&afull[c & 1])) : "memory");
       }
-      if (!ok) atomicOr((int*)&s_fail, 1);
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      // builders' barrier with the stop decision reduced over all four warps,
-      // so that they leave the loop together
-      const uint32_t stop_in = (!ok || *fail) ? 1u : 0u;
-      uint32_t stop;
-      asm volatile(
-          "{\n .reg .pred q, r;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred r, 1, 128, q;\n selp.u32 %0, 1, 0, r;\n}\n"
-          : "=r"(stop)
-          : "r"(stop_in)
-          : "memory");
-      if (stop) break;
-      // this chunk's segments: slot per block, and the ones ending here
-      int slot_kb[4];
+      // the pieces that ended in the previous chunk, while the issuer works on this one
+      if (!drain()) {
+        atomicOr((int*)&s_fail, 1);
+        break;
+      }
+      // this chunk's pieces: slot per block, and the ones ending here
 #pragma unroll
       for (int kb = 0; kb < 4; ++kb) {
         if (fls[kb] & kStart) {
           cur_slot = segc % kNacc;
           ++segc;
         }
-        slot_kb[kb] = cur_slot;
         if (fls[kb] & kEnd) {
           pend_code[npend] = cds[kb];
           pend_slot[npend] = cur_slot;
@@ -436,30 +510,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
           ++npend;
         }
       }
-      if (tid == 0) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t acol = (uint32_t)((c & 1) * 64);
-        const uint64_t dh = sdesc_sw128(smem_u32(st));
-        const uint64_t dl = sdesc_sw128(smem_u32(st + NP * 128));
-        for (int kb = 0; kb < nvb; ++kb) {
-          const uint32_t d = tmem + dcol0 + (uint32_t)(slot_kb[kb] * NP);
-          const uint32_t ah = tmem + acol + 8 * kb, al = ah + 32;
-          const uint64_t k = (uint64_t)(2 * kb);  // +32 bytes per K-step of 8
-          mma_tf32_ts(d, ah, dh + k, idesc, (fls[kb] & kStart) ? 0u : 1u);
-          mma_tf32_ts(d, ah, dl + k, idesc, 1u);
-          mma_tf32_ts(d, al, dh + k, idesc, 1u);
-          if (fls[kb] & kEnd) mma_commit(&accf[slot_kb[kb]]);
-        }
-        mma_commit(&empty[s]);
-        mma_commit(&abar[c & 1]);
-      }
     }
     if (!*fail)
       if (!drain()) atomicOr((int*)&s_fail, 1);
   }
 
   // no MMA may be in flight when the tensor memory is released
-  if (tid == 0) {
+  if (tid == 8 * 32) {
     mma_commit(fin);
     if (!mbar_wait(fin, 0)) atomicOr((int*)&s_fail, 1);
   }
@@ -678,12 +735,17 @@ void tk_ttmc_tc_launch(tucker_ctx* c, int n, void* const* F, const int* ldF, con
   a.Zpart = (float*)c->Zpart;
   a.err = c->err;
   a.cap = c->wait_cap;
-  // stages | barriers (2 kStages + 2 + kNacc + 1) | TMEM slot (8 B) | running sums (NP x 128 floats)
-  const size_t smem = 1024 + (size_t)kStages * a.stage_bytes + (2 * kStages + 2 + kNacc + 2) * 8 + (size_t)a.NP * 128 * 4;
+  // stages | barriers (2 kStages + 4 + 2 kNacc + 1) | TMEM slot (8 B) | running sums (NP x 128 floats)
+  const size_t smem = 1024 + (size_t)kStages * a.stage_bytes + (2 * kStages + 4 + 2 * kNacc + 2) * 8 +
+                      (size_t)a.NP * 128 * 4;
   const int nvr = std::max(a.nv[0], std::max(a.nv[1], a.nv[2]));
-  void (*kern)(const TcArgs) = nvr <= 2 ? k_ttmc_tc<2, 4> : nvr <= 3 ? k_ttmc_tc<3, 4> : nvr <= 4 ? k_ttmc_tc<4, 4>
-                                                                                                   : k_ttmc_tc<8, 2>;
+  // loader registers: kU chunks' rows of kNVR vectors within the 96 registers of two CTAs per SM
+  void (*kern)(const TcArgs) = nvr <= 2 ? k_ttmc_tc<2, 4> : nvr <= 3 ? k_ttmc_tc<3, 4> : nvr <= 4 ? k_ttmc_tc<4, 2>
+                                                                                                   : k_ttmc_tc<8, 1>;
   TK_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // two CTAs per SM when their tensor memory fits (N = 16): each CTA has one
+  // MMA-issuing thread, and a tcgen05.mma of this size costs its issuer far
+  // more cycles than the tensor core needs for it, so issuers run side by side
   const int per_sm = a.tmem_cols <= 256 ? 2 : 1;
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * c->sm_count, md.tc_nblk));
   kern<<<(unsigned)grid, kTcThreads, smem, s>>>(a);

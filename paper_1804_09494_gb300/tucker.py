@@ -41,7 +41,7 @@ FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void
 class Opts(ctypes.Structure):
     _fields_ = [("prec", _I32), ("P_bins", _I32), ("gauss_seidel", _I32), ("timing", _I32),
                 ("wait_cap", _I32), ("ttm_path", _I32), ("alloc", ALLOC_FN), ("free", FREE_FN),
-                ("alloc_user", _VP), ("reserved", _I32 * 4)]
+                ("alloc_user", _VP), ("svd", _I32), ("reserved", _I32 * 3)]
 
 
 def torch_allocator(device):
@@ -143,10 +143,12 @@ class Tucker:
     vals : (nnz,) float32 (prec "fp32", "tf32x3" or "bf16x3") or float64 (prec="fp64") CUDA tensor
     L, K : mode lengths and core lengths
     ttm_path : "auto" (the tensor-core TTM-chain where it applies) or "cuda_cores"
+    svd : "exact" (leading subspace of Z through its Gram matrix) or "lanczos"
+          (the paper's Lanczos bidiagonalisation with 2K steps)
     """
 
     def __init__(self, idx, vals, L, K, prec="fp32", P_bins=0, gauss_seidel=False, timing=False,
-                 wait_cap=0, allocator="torch", ttm_path="auto"):
+                 wait_cap=0, allocator="torch", ttm_path="auto", svd="exact"):
         self.lib = load_library()
         if not torch.cuda.is_available():
             raise RuntimeError("libtucker needs a CUDA device")
@@ -172,6 +174,9 @@ class Tucker:
         if ttm_path not in ("auto", "cuda_cores"):
             raise ValueError('ttm_path must be "auto" or "cuda_cores"')
         opts.ttm_path = 0 if ttm_path == "auto" else 1
+        if svd not in ("exact", "lanczos"):
+            raise ValueError('svd must be "exact" or "lanczos"')
+        opts.svd = 0 if svd == "exact" else 1
         # device memory from torch's caching allocator (allocator="torch"), or
         # the library's own cudaMalloc (allocator=None); the callbacks live as
         # long as the context

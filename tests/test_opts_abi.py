@@ -11,7 +11,7 @@ import pytest
 from paper_1804_09494_gb300 import tucker as T
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-FIELDS = ["prec", "P_bins", "gauss_seidel", "timing", "wait_cap", "ttm_path", "alloc", "free", "alloc_user", "reserved"]
+FIELDS = ["prec", "P_bins", "gauss_seidel", "timing", "wait_cap", "ttm_path", "alloc", "free", "alloc_user", "svd", "reserved"]
 
 
 def test_opts_layout_matches_header():
