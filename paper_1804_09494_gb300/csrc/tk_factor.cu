@@ -1806,7 +1806,8 @@ void factor_impl(tucker_ctx* c, int n, const void* Zv, void* F_out, int ldF_out,
     gram_done = true;
   }
   if constexpr (sizeof(T) == 4) {
-    if (!c->gram_bf16 && tk_gram_tc_supported(Khat) && ((uintptr_t)Z % 16 == 0)) {
+    if (gram_done) {
+    } else if (!c->gram_bf16 && tk_gram_tc_supported(Khat) && ((uintptr_t)Z % 16 == 0)) {
       // tensor cores: per-CTA partials, reduced and symmetrised in FP64
       tk_gram_tc(c, (const float*)Z, R, Khat, (float*)ws->Wpart, ws->Wpart_elems, ws->W, s);
       tk_launched(c, PH_GRAM, 2);
