@@ -1032,7 +1032,8 @@ __host__ __device__ inline int eig_v4_ld(int n) {
 }
 __host__ __device__ inline size_t eig_v4_smem(int n, int K) {
   const int ld = eig_v4_ld(n), np = (n + 3) & ~3;
-  size_t e = (size_t)3 * n * ld + (size_t)n * K + (size_t)5 * np;
+  // the n x K block is padded to whole float4s: the vectors after it are read as float4
+  size_t e = (size_t)3 * n * ld + (((size_t)n * K + 3) & ~(size_t)3) + (size_t)5 * np;
   if ((size_t)6 * K * n > (size_t)n * ld) e += (size_t)6 * K * n;
   return (size_t)2 * K * (K + 1) * sizeof(double) + e * sizeof(float);
 }
@@ -1054,7 +1055,7 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_v4(const EigArgs<float
   float* Q = A + (size_t)n * ld;          // n x ld, Q[r][k]
   float* QT = Q + (size_t)n * ld;         // m x ld, QT[k][r]
   float* Xs = QT + (size_t)m * ld;
-  float* ws = Xs + (size_t)n * K;
+  float* ws = Xs + (((size_t)n * K + 3) & ~(size_t)3);  // 16-byte aligned (float4 reads)
   float* hs = ws + np;
   float* ta = hs + np;
   float* tb = ta + np;

@@ -36,6 +36,9 @@ def aligned_core(G, F, Fo, K):
 @pytest.mark.parametrize("L,nnz,zipf,K", [((200, 150, 100), 20_000, None, (8, 8, 8)),
                                          ((3000, 2000, 500), 200_000, (1.1, 1.1, 1.1), (10, 10, 10)),
                                          ((400, 300, 60, 20), 100_000, (1.2, 1.2, None, None), (6, 5, 4, 3)),
+                                         # Khat K odd in every mode (35 x 3, 21 x 5, 15 x 7): the eigensolver's
+                                         # shared-memory blocks after the n x K one stay 16-byte aligned
+                                         ((300, 200, 100), 30_000, (1.1, 1.1, 1.1), (3, 5, 7)),
                                          # Khat = 256, 512, 1000: the Gram in 128 x 128 blocks (ragged last block at 1000)
                                          ((2000, 1500, 300), 60_000, (1.1, 1.1, 1.1), (16, 16, 16)),
                                          ((500, 500, 80, 30), 80_000, (1.3, 1.3, 1.3, 1.3), (8, 8, 8, 8)),
