@@ -56,7 +56,7 @@ def test_gradient_steps_reduce_the_nonzero_loss(prec):
         loss = ((vals - xhat) ** 2).sum()
         loss.backward()
         opt.step()
-        losses.append(float(loss))
+        losses.append(float(loss.detach()))
     tk.close()
     assert all(np.isfinite(losses))
     assert losses[-1] < 1e-4 * losses[0], (losses[0], losses[-1])
