@@ -98,7 +98,11 @@ typedef struct {
   int32_t ttm_path;      /* 0 = the tensor-core TTM-chain where it applies (4-mode FP32   *
                           * contexts with 32 <= K_a K_b <= 128, K_c <= 48, Khat >= 256,    *
                           * a < b < c the other modes; it keeps a second, block-padded     *
-                          * copy of those modes' elements), 1 = CUDA cores only           */
+                          * copy of those modes' elements), 1 = CUDA cores only,          *
+                          * 2 = CUDA cores, fiber-factored where the fiber mode is the     *
+                          * second remaining mode (3-mode FP32 contexts, exact tiles:      *
+                          * K_a x K_b of 10 x 10, 8 x 8, 16 x 16): each element adds       *
+                          * val F_a into a fiber sum, F_b is gathered once per fiber      */
   tucker_alloc_fn alloc; /* NULL: the library calls cudaMalloc / cudaFree itself          */
   tucker_free_fn free;   /* must be non-NULL exactly when alloc is                        */
   void* alloc_user;      /* passed to alloc and free                                      */

@@ -220,7 +220,7 @@ tucker_status tucker_init(tucker_t* out, int N, const int64_t* L, const int32_t*
       tk_throw(TUCKER_ERR_ARG, "unknown precision");
     if (o.P_bins < 0) tk_throw(TUCKER_ERR_ARG, "P_bins must be >= 0");
     if (o.wait_cap < -1) tk_throw(TUCKER_ERR_ARG, "wait_cap must be >= -1");
-    if (o.ttm_path != 0 && o.ttm_path != 1) tk_throw(TUCKER_ERR_ARG, "ttm_path must be 0 or 1");
+    if (o.ttm_path < 0 || o.ttm_path > 2) tk_throw(TUCKER_ERR_ARG, "ttm_path must be 0, 1 or 2");
     for (int i = 0; i < 3; ++i)
       if (o.reserved[i]) tk_throw(TUCKER_ERR_ARG, "reserved option fields must be zero");
     if (o.svd != 0 && o.svd != 1) tk_throw(TUCKER_ERR_ARG, "svd must be 0 or 1");

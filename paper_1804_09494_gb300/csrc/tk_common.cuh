@@ -126,7 +126,8 @@ struct tucker_ctx {
   bool gram_bf16 = false;   // TUCKER_BF16X3: the Gram in split BF16
   size_t esz = 4;
   int gauss_seidel = 0;
-  int ttm_path = 0;         // 0: tensor-core TTM-chain where eligible, 1: CUDA cores only
+  int ttm_path = 0;         // 0: tensor-core TTM-chain where eligible, 1: CUDA cores only,
+                            // 2: CUDA cores, fiber-factored where it applies
   int svd_lanczos = 0;      // factor update: 0 exact leading subspace (Gram), 1 Lanczos bidiagonalisation
   int timing = 0;
   int sm_count = 0;

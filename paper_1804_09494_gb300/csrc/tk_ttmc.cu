@@ -22,6 +22,14 @@
 // coordinates in the copy are popularity labels and each slice lists its
 // elements by the label of the fiber-mode coordinate, so all threads sweep the
 // hot factor rows together.
+//
+// Fiber-factored form (an option): when the fiber mode is b, consecutive
+// elements of a slice that share F_b's row form a fiber, and
+//     sum_fiber val F_a (x) F_b = (sum_fiber val F_a) (x) F_b,
+// so each element adds val F_a into a fiber sum (K_a FMAs) and the F_b row is
+// gathered, and the sum expanded into the slice tile, once per fiber.  The
+// fiber ends differ between the threads of a warp, so the expansion is taken
+// by the whole warp almost every step; the form saves gathers, not FMAs.
 #include <algorithm>
 
 #include "tk_common.cuh"
@@ -190,7 +198,7 @@ constexpr uint32_t kNoCode = 0xFFFFFFFFu;  // no slice yet (row codes stay below
 // D elements' rows in flight per thread; OUTER: the tensor has outer modes
 // (more than two other modes), whose scalings are gathered with the rows;
 // OVR: values come from a caller's array (by original element id).
-template <typename T, int MA, int MB, bool EA, bool EB, int D, bool OUTER, bool OVR>
+template <typename T, int MA, int MB, bool EA, bool EB, int D, bool OUTER, bool OVR, bool FIB = false>
 __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
   using V = typename VecT<T>::type;
   constexpr int W = VecT<T>::W;
@@ -229,6 +237,12 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
 #pragma unroll
   for (int i = 0; i < MA * MB; ++i) acc[i] = T(0);
   uint32_t cur = kNoCode;
+  T sf[FIB ? MA : 1], Bf[FIB ? MB : 1];
+  int cur_lb = -1;
+  if constexpr (FIB) {
+#pragma unroll
+    for (int i = 0; i < MA; ++i) sf[i] = T(0);
+  }
 
   // writes the accumulator to the row (or split slot) of `code` when `on`, and
   // clears it either way
@@ -276,6 +290,8 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
   T A[D][RA], B[D][RB];
   T v[D], fq[D][NQ];
   uint32_t code[D];
+  int lbk[FIB ? D : 1];
+  int prev_lb = -1;
   auto issue = [&](int d, int k) __attribute__((always_inline)) {
     // row code and value of element k, D ahead of use, with its rows
     {
@@ -296,7 +312,13 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
         A[d][u * W + 1] = t.y;
       }
     }
-    if (twob) {
+    bool needB = true;
+    if constexpr (FIB) {
+      lbk[d] = nlb[d];
+      needB = nlb[d] != prev_lb;
+      prev_lb = nlb[d];
+    }
+    if (twob && needB) {
       const int64_t rb = (int64_t)nlb[d] * a.ld[1] + j0;
 #pragma unroll
       for (int u = 0; u < NB; ++u) {
@@ -333,7 +355,32 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
       // refill the slot with element j+d+D's rows and element j+d+2D's
       // coordinates (the other D-1 slots stay in flight meanwhile; no copies,
       // so the loop carries every slot in the same registers)
-      if (j + d < len) {
+      if (FIB && j + d < len) {
+        const uint32_t cd = code[d];
+        const int lb = lbk[FIB ? d : 0];
+        if (cd != cur || lb != cur_lb) {
+          if (cur != kNoCode) {
+#pragma unroll
+            for (int jj = 0; jj < MB; ++jj)
+#pragma unroll
+              for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(sf[i], Bf[jj], acc[i + MA * jj]);
+          }
+#pragma unroll
+          for (int i = 0; i < MA; ++i) sf[i] = T(0);
+          if (cd != cur) {
+            flush_clear(cur == kNoCode ? 0u : cur, cur != kNoCode);
+            cur = cd;
+          }
+          if (lb != cur_lb) {
+#pragma unroll
+            for (int jj = 0; jj < MB; ++jj) Bf[jj] = B[d][jj];
+            cur_lb = lb;
+          }
+        }
+        const T vcf = v[d];
+#pragma unroll
+        for (int i = 0; i < MA; ++i) sf[i] = fma(A[d][i], vcf, sf[i]);
+      } else if (!FIB && j + d < len) {
         const uint32_t cd = code[d];
         if (cd != cur) {
           flush_clear(cur == kNoCode ? 0u : cur, cur != kNoCode);
@@ -353,6 +400,14 @@ __global__ void __launch_bounds__(128, 1) k_ttmc_fwd(const TtmcArgs<T> a) {
       }
       issue(d, j + d + D);
       fetch(d, j + d + 2 * D);
+    }
+  }
+  if constexpr (FIB) {
+    if (len > 0) {
+#pragma unroll
+      for (int jj = 0; jj < MB; ++jj)
+#pragma unroll
+        for (int i = 0; i < MA; ++i) acc[i + MA * jj] = fma(sf[i], Bf[jj], acc[i + MA * jj]);
     }
   }
   if (len > 0) flush_clear(cur, 1);
@@ -790,6 +845,20 @@ KernelT<double> fwd_kernel<double>(int id, bool outer, bool ovr) {
   }
 }
 #undef TK_FWD_PICK
+// Fiber-factored forms (FP32, exact tiles, two remaining modes): one element
+// fewer in flight for the fiber sum and the current fiber's row
+KernelT<float> fib_kernel(int id, bool ovr) {
+  switch (id) {
+    case 0: return ovr ? k_ttmc_fwd<float, 10, 10, true, true, 3, false, true, true>
+                       : k_ttmc_fwd<float, 10, 10, true, true, 3, false, false, true>;
+    case 1: return ovr ? k_ttmc_fwd<float, 8, 8, true, true, 3, false, true, true>
+                       : k_ttmc_fwd<float, 8, 8, true, true, 3, false, false, true>;
+    case 2: return ovr ? k_ttmc_fwd<float, 16, 8, true, true, 2, false, true, true>
+                       : k_ttmc_fwd<float, 16, 8, true, true, 2, false, false, true>;
+    default: return nullptr;
+  }
+}
+
 template <typename T>
 using BwdKernelT = void (*)(TtmcArgs<T>, int, BwdOut<T>);
 // rows in flight per thread for the adjoint: the cotangent block plus D
@@ -904,7 +973,15 @@ void forward_impl(tucker_ctx* c, int n, void* const* F, const int* ldF, const vo
   if (md.tc) {
     tk_ttmc_tc_launch(c, n, F, ldF, vals_override, Z, s);
   } else {
-    fwd_kernel<T>(pl.tile_id, pl.nother > 2, vals_override != nullptr)<<<blocks_for(md, pl.G), 128, 0, s>>>(a);
+    KernelT<T> kern = fwd_kernel<T>(pl.tile_id, pl.nother > 2, vals_override != nullptr);
+    if constexpr (sizeof(T) == 4) {
+      // the fiber-factored form where it applies (tucker_opts.ttm_path = 2)
+      if (c->ttm_path == 2 && pl.nother == 2 && c->fiber[n] == pl.others[1]) {
+        KernelT<float> f = fib_kernel(pl.tile_id, vals_override != nullptr);
+        if (f) kern = f;
+      }
+    }
+    kern<<<blocks_for(md, pl.G), 128, 0, s>>>(a);
     TK_CUDA(cudaGetLastError());
   }
   tk_phase_end(c, s);

@@ -142,7 +142,8 @@ class Tucker:
     idx  : (N, nnz) int32 CUDA tensor of 0-based coordinates (distinct)
     vals : (nnz,) float32 (prec "fp32", "tf32x3" or "bf16x3") or float64 (prec="fp64") CUDA tensor
     L, K : mode lengths and core lengths
-    ttm_path : "auto" (the tensor-core TTM-chain where it applies) or "cuda_cores"
+    ttm_path : "auto" (the tensor-core TTM-chain where it applies), "cuda_cores", or "fiber"
+               (CUDA cores, fiber-factored where the fiber mode is the second remaining mode)
     svd : "exact" (leading subspace of Z through its Gram matrix) or "lanczos"
           (the paper's Lanczos bidiagonalisation with 2K steps)
     """
@@ -171,9 +172,10 @@ class Tucker:
         opts.gauss_seidel = int(bool(gauss_seidel))
         opts.timing = int(bool(timing))
         opts.wait_cap = int(wait_cap)
-        if ttm_path not in ("auto", "cuda_cores"):
-            raise ValueError('ttm_path must be "auto" or "cuda_cores"')
-        opts.ttm_path = 0 if ttm_path == "auto" else 1
+        paths = {"auto": 0, "cuda_cores": 1, "fiber": 2}
+        if ttm_path not in paths:
+            raise ValueError('ttm_path must be "auto", "cuda_cores" or "fiber"')
+        opts.ttm_path = paths[ttm_path]
         if svd not in ("exact", "lanczos"):
             raise ValueError('svd must be "exact" or "lanczos"')
         opts.svd = 0 if svd == "exact" else 1

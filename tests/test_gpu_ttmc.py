@@ -191,3 +191,38 @@ def test_invalid_inputs_are_rejected():
     with pytest.raises(TuckerError) as ei:
         make(c, (2, 2, 2), "fp32", P_bins=-1)
     assert ei.value.status == "ERR_ARG"
+
+
+FIBER_CASES = [
+    # 3-mode, exact tiles (K_a x K_b = 8 x 8, 10 x 10, 16 x 16); in every mode the
+    # fiber mode (the other mode with fewer slices) is the second remaining mode
+    ("uniform-3d-k8", (200, 150, 100), 20_000, None, "uniform", (8, 8, 8)),
+    ("zipf-3d-k10", (3000, 2000, 500), 200_000, (1.1, 1.1, 1.1), "lognormal", (10, 10, 10)),
+    ("zipf-3d-k16", (2000, 1500, 300), 60_000, (1.1, 1.1, 1.1), "uniform", (16, 16, 16)),
+]
+
+
+@pytest.mark.parametrize("P", [0, 64])
+@pytest.mark.parametrize("name,L,nnz,zipf,values,K", FIBER_CASES, ids=[c[0] for c in FIBER_CASES])
+def test_fiber_factored_ttm_chain_matches_oracle(name, L, nnz, zipf, values, K, P):
+    """The fiber-factored form (sum over a fiber of val F_a, expanded with the
+    fiber's F_b row once) against the oracle, with the default bin count and
+    with few bins (most heavy slices split)."""
+    c = case(L, nnz, zipf, values, seed=12)
+    tk = make(c, K, "fp32", ttm_path="fiber", P_bins=P)
+    Fd, Fo = factors(L, K, 6, "fp32")
+    for n in range(3):
+        check_ttm(tk, c, Fd, Fo, n, "fp32")
+    tk.close()
+
+
+def test_fiber_factored_ttm_chain_value_override():
+    c = case((400, 300, 200), 30_000, (1.1, 1.1, 1.1), "uniform", seed=13)
+    K = (10, 10, 10)
+    tk = make(c, K, "fp32", ttm_path="fiber")
+    Fd, Fo = factors(c["L"], K, 3, "fp32")
+    v = np.random.default_rng(2).standard_normal(len(c["vals"])).astype(np.float32).astype(np.float64)
+    vd = torch.from_numpy(v).to(DT["fp32"]).cuda()
+    for n in range(3):
+        check_ttm(tk, c, Fd, Fo, n, "fp32", vals=vd, vals_np=v)
+    tk.close()
