@@ -11,7 +11,11 @@
 // block of 8 elements is one MMA step (M = 128, N = 16..48, K = 8).  In FP32
 // accuracy: x = xh + xl and y = yh + yl with xh, yh the TF32-truncated values
 // and xl, yl the exact FP32 rests, and Z[l] += xh yh^T + xh yl^T + xl yh^T
-// (three MMAs; xl yl^T is below FP32 resolution).
+// (xl yl^T is below FP32 resolution).  The yh and yl tiles lie one after the
+// other in shared memory, so the first two terms are one MMA of twice the
+// width, xh [yh | yl]^T, into an accumulator of 2N columns, and xl yh^T adds
+// into its first N columns: two MMAs per block, whose issue cost does not
+// grow with N.
 //
 // Layout: a second copy of the mode's elements, made at init from the Lite
 // copy: every bin's elements contiguous, every segment of a bin (a whole
@@ -38,14 +42,14 @@
 //     add it to the segment's running sum, and at the segment's end store its
 //     row of Z (or the split piece's partial, added by the fix-up in bin
 //     order, as for the CUDA-core kernel), then release the slot;
-//   * warp 8 issues the MMAs: per block, the accumulator slot of its piece (8
-//     slots of N columns, round robin, a slot reused only once it has been
-//     read back) and three MMAs; where a piece ends, a commit to the slot's
-//     mbarrier.
-// A tcgen05.mma of this shape (M = 128, N = 16, K = 8) occupies its issuing
-// thread for far longer than the tensor core computes it, so the issuer sets
-// the pace: two CTAs share an SM (256 tensor-memory columns each) to run two
-// issuers side by side.
+//   * warp 8 issues the MMAs: per block, the accumulator slot of its piece (up
+//     to 8 slots of 2N columns, round robin, a slot reused only once it has
+//     been read back) and two MMAs; where a piece ends, a commit to the slot's
+//     mbarrier.  The drain adds the slot's two halves.
+// A tcgen05.mma of this shape (M = 128, N = 16..96, K = 8) occupies its
+// issuing thread for far longer than the tensor core computes it (about 50-70
+// cycles, whatever N): two CTAs share an SM (256 tensor-memory columns each)
+// to run two issuers side by side.
 // Every mbarrier wait is bounded (clock and the context's poll cap); a
 // timeout sets TK_DEV_ERR_TIMEOUT, every role leaves its loop, the CTA waits
 // (bounded) for its MMAs in flight and releases its tensor memory.
@@ -61,7 +65,7 @@ using namespace tk_tc;
 constexpr int kTcThreads = 288;  // warps 0-3 build and drain, 4-7 load, 8 issues the MMAs
 constexpr int kChunk = 32;       // elements per stage: 4 blocks of 8
 constexpr int kStages = 8;
-constexpr int kNacc = 8;         // accumulator slots
+constexpr int kNacc = 8;         // accumulator slots at most
 constexpr int kRowStride = 36;   // floats per staged F_a / F_b row (144 B: rows on different banks)
 constexpr uint32_t kCodeSplit = 0x80000000u;
 constexpr uint8_t kStart = 1, kEnd = 2, kFinal = 4;
@@ -87,6 +91,7 @@ struct TcArgs {
   int stage_bytes;   // multiple of 1024
   int off_va, off_bb, off_info;
   int tmem_cols;
+  int nacc;  // accumulator slots of 2 NP columns after the 128 columns of A
   float* Z;
   float* Zpart;
   int* err;
@@ -141,12 +146,10 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-      : "r"(taddr));
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
@@ -345,10 +348,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
     // ------------------------------------------------------------ MMA issuer
     // Per chunk, once the builders have written its A: the slot of each
     // block's accumulator (a new one where a piece starts, after the builders
-    // have read back its previous piece), three MMAs per block, a commit to
+    // have read back its previous piece), two MMAs per block, a commit to
     // the slot's barrier where a piece ends, then the stage and the A buffer
     // are released by commits.
-    const uint32_t idesc = idesc_tf32(NP);
+    const uint32_t idesc = idesc_tf32(NP), idesc2 = idesc_tf32(2 * NP);
     const uint32_t dcol0 = 128;
     int segc = 0, cur_slot = 0;
     uint32_t used = 0, epar = 0;
@@ -361,12 +364,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
         const uint32_t* info = (const uint32_t*)(st + a.off_info);
         const int nvb = (int)min((int64_t)4, B1 - B0 - 4 * (int64_t)c);
         const uint32_t acol = (uint32_t)((c & 1) * 64);
-        const uint64_t dh = sdesc_sw128(smem_u32(st));
-        const uint64_t dl = sdesc_sw128(smem_u32(st + NP * 128));
+        const uint64_t dh = sdesc_sw128(smem_u32(st));  // yh rows, then yl rows
         for (int kb = 0; kb < nvb; ++kb) {
           const uint32_t fl = info[4 + kb];
           if (fl & kStart) {
-            cur_slot = segc % kNacc;
+            cur_slot = segc % a.nacc;
             ++segc;
             if (used & (1u << cur_slot)) {
               if (!wait_warp(&acce[cur_slot], (epar >> cur_slot) & 1u, a.cap, fail)) {
@@ -378,13 +380,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
             used |= 1u << cur_slot;
           }
           if (lane == 0) {
-            const uint32_t d = tmem + dcol0 + (uint32_t)(cur_slot * NP);
+            const uint32_t d = tmem + dcol0 + (uint32_t)(cur_slot * 2 * NP);
             const uint32_t ah = tmem + acol + 8 * kb, al = ah + 32;
             const uint64_t k = (uint64_t)(2 * kb);  // +32 bytes per K-step of 8
             const uint32_t en = (fl & kStart) ? 0u : 1u;
-            mma_tf32_ts(d, ah, dh + k, idesc, en);
-            mma_tf32_ts(d, ah, dl + k, idesc, 1u);
-            mma_tf32_ts(d, al, dh + k, idesc, 1u);
+            mma_tf32_ts(d, ah, dh + k, idesc2, en);  // [xh yh | xh yl]
+            mma_tf32_ts(d, al, dh + k, idesc, 1u);   // + xl yh in the first half
             if (fl & kEnd) mma_commit(&accf[cur_slot]);
           }
           __syncwarp();
@@ -426,15 +427,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
         const uint32_t cd = pend_code[p];
         const bool fin_p = pend_final[p];
         float* dst = (cd & kCodeSplit) ? a.Zpart + (int64_t)(cd & ~kCodeSplit) * a.Khat : a.Z + (int64_t)cd * a.Khat;
-        for (int n0 = 0; n0 < NP; n0 += 16) {
-          uint32_t r[16];
-          tmem_ld16(lane_base + dcol0 + (uint32_t)(sl * NP + n0), r);
+        for (int n0 = 0; n0 < NP; n0 += 8) {
+          uint32_t r[8], r2[8];
+          tmem_ld8(lane_base + dcol0 + (uint32_t)(sl * 2 * NP + n0), r);
+          tmem_ld8(lane_base + dcol0 + (uint32_t)(sl * 2 * NP + NP + n0), r2);
           if (act) {
 #pragma unroll
-            for (int t = 0; t < 16; ++t) {
+            for (int t = 0; t < 8; ++t) {
               const int nn = n0 + t;
               if (nn < a.Nu) {
-                float x = __uint_as_float(r[t]);
+                float x = __uint_as_float(r[t]) + __uint_as_float(r2[t]);
                 if (has_run) x += run[nn * 128 + m];
                 if (fin_p) dst[m + (int64_t)a.Mu * nn] = x;
                 else run[nn * 128 + m] = x;
@@ -500,7 +502,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
 #pragma unroll
       for (int kb = 0; kb < 4; ++kb) {
         if (fls[kb] & kStart) {
-          cur_slot = segc % kNacc;
+          cur_slot = segc % a.nacc;
           ++segc;
         }
         if (fls[kb] & kEnd) {
@@ -632,12 +634,15 @@ int stage_bytes_for(int K0, int K1, int NP, int* off_va, int* off_bb, int* off_i
   return (off + kTcStageAlign - 1) / kTcStageAlign * kTcStageAlign;
 }
 
+// A buffers in columns [0, 128), then at least four accumulator slots of
+// 2 NP columns (NP = 16: 256 columns, two CTAs per SM)
 int tmem_cols_for(int NP) {
-  const int need = 128 + kNacc * NP;
+  const int need = 128 + 4 * 2 * NP;
   int c = 32;
   while (c < need) c *= 2;
   return c;
 }
+int nacc_for(int NP, int cols) { return std::min(kNacc, (cols - 128) / (2 * NP)); }
 
 void others_of(const tucker_ctx* c, int n, int* o) {
   int k = 0;
@@ -731,6 +736,7 @@ void tk_ttmc_tc_launch(tucker_ctx* c, int n, void* const* F, const int* ldF, con
   a.Khat = md.Khat;
   a.stage_bytes = stage_bytes_for(a.K[0], a.K[1], a.NP, &a.off_va, &a.off_bb, &a.off_info);
   a.tmem_cols = tmem_cols_for(a.NP);
+  a.nacc = nacc_for(a.NP, a.tmem_cols);
   a.Z = (float*)Z;
   a.Zpart = (float*)c->Zpart;
   a.err = c->err;
