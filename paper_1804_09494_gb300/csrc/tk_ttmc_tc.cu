@@ -128,6 +128,17 @@ __device__ __forceinline__ bool wait_warp(const uint64_t* bar, uint32_t parity, 
   }
 }
 
+// One thread's bounded wait (the MMA issuer works alone), with the same limits.
+__device__ __forceinline__ bool wait_one(const uint64_t* bar, uint32_t parity, int cap, const volatile int* fail) {
+  if (cap < 0) return false;
+  const uint32_t addr = smem_u32(bar);
+  const long long t0 = clock64();
+  for (int polls = 1;; ++polls) {
+    if (mbar_try(addr, parity)) return true;
+    if (*fail != 0 || clock64() - t0 > kWaitCycles || (cap > 0 && polls >= cap)) return false;
+  }
+}
+
 __device__ __forceinline__ void mma_tf32_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -173,8 +184,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
   unsigned char* sm = smraw + ((1024 - (smem_u32(smraw) & 1023)) & 1023);
   uint64_t* full = (uint64_t*)(sm + kStages * a.stage_bytes);
   uint64_t* empty = full + kStages;
-  uint64_t* abar = empty + kStages;  // 2: A buffer free (MMAs of its chunk done)
-  uint64_t* afull = abar + 2;        // 2: A buffer written (4 builder warps)
+  // empty[s] also frees the A buffer of the stage's chunk: its MMAs are done
+  uint64_t* afull = empty + kStages;  // 2: A buffer written (4 builder warps)
   uint64_t* accf = afull + 2;        // kNacc: accumulator of the slot complete
   uint64_t* acce = accf + kNacc;     // kNacc: slot read back (4 builder warps)
   uint64_t* fin = acce + kNacc;
@@ -197,10 +208,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "r"(128));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty[i])), "r"(1));
     }
-    for (int i = 0; i < 2; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&abar[i])), "r"(1));
+    for (int i = 0; i < 2; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&afull[i])), "r"(4));
-    }
     for (int i = 0; i < kNacc; ++i) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&accf[i])), "r"(1));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&acce[i])), "r"(4));
@@ -349,37 +358,39 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
     // Per chunk, once the builders have written its A: the slot of each
     // block's accumulator (a new one where a piece starts, after the builders
     // have read back its previous piece), two MMAs per block, a commit to
-    // the slot's barrier where a piece ends, then the stage and the A buffer
-    // are released by commits.
-    const uint32_t idesc = idesc_tf32(NP), idesc2 = idesc_tf32(2 * NP);
-    const uint32_t dcol0 = 128;
-    int segc = 0, cur_slot = 0;
-    uint32_t used = 0, epar = 0;
-    for (int c = 0; c < nchunks; ++c) {
-      const int s = c % kStages;
-      unsigned char* st = sm + s * a.stage_bytes;
-      bool ok = wait_warp(&afull[c & 1], (uint32_t)((c >> 1) & 1), a.cap, fail);
-      if (ok) {
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t* info = (const uint32_t*)(st + a.off_info);
-        const int nvb = (int)min((int64_t)4, B1 - B0 - 4 * (int64_t)c);
-        const uint32_t acol = (uint32_t)((c & 1) * 64);
-        const uint64_t dh = sdesc_sw128(smem_u32(st));  // yh rows, then yl rows
-        for (int kb = 0; kb < nvb; ++kb) {
-          const uint32_t fl = info[4 + kb];
-          if (fl & kStart) {
-            cur_slot = segc % a.nacc;
-            ++segc;
-            if (used & (1u << cur_slot)) {
-              if (!wait_warp(&acce[cur_slot], (epar >> cur_slot) & 1u, a.cap, fail)) {
-                ok = false;
-                break;
+    // the slot's barrier where a piece ends, then one commit releases the
+    // stage and the A buffer.
+    // Lane 0 alone: MMAs and commits are issued by one thread.
+    if (lane == 0) {
+      const uint32_t idesc = idesc_tf32(NP), idesc2 = idesc_tf32(2 * NP);
+      const uint32_t dcol0 = 128;
+      int segc = 0, cur_slot = 0;
+      uint32_t used = 0, epar = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        const int s = c % kStages;
+        unsigned char* st = sm + s * a.stage_bytes;
+        bool ok = wait_one(&afull[c & 1], (uint32_t)((c >> 1) & 1), a.cap, fail);
+        if (ok) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t* info = (const uint32_t*)(st + a.off_info);
+          const int nvb = (int)min((int64_t)4, B1 - B0 - 4 * (int64_t)c);
+          const uint32_t acol = (uint32_t)((c & 1) * 64);
+          const uint64_t dh = sdesc_sw128(smem_u32(st));  // yh rows, then yl rows
+          for (int kb = 0; kb < nvb; ++kb) {
+            const uint32_t fl = info[4 + kb];
+            if (fl & kStart) {
+              cur_slot = segc % a.nacc;
+              ++segc;
+              if (used & (1u << cur_slot)) {
+                if (!wait_one(&acce[cur_slot], (epar >> cur_slot) & 1u, a.cap, fail)) {
+                  ok = false;
+                  break;
+                }
+                epar ^= 1u << cur_slot;
+                asm volatile("tcgen05.fence::after_thread_sync;");
               }
-              epar ^= 1u << cur_slot;
+              used |= 1u << cur_slot;
             }
-            used |= 1u << cur_slot;
-          }
-          if (lane == 0) {
             const uint32_t d = tmem + dcol0 + (uint32_t)(cur_slot * 2 * NP);
             const uint32_t ah = tmem + acol + 8 * kb, al = ah + 32;
             const uint64_t k = (uint64_t)(2 * kb);  // +32 bytes per K-step of 8
@@ -388,19 +399,15 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
             mma_tf32_ts(d, al, dh + k, idesc, 1u);   // + xl yh in the first half
             if (fl & kEnd) mma_commit(&accf[cur_slot]);
           }
-          __syncwarp();
+          if (ok) mma_commit(&empty[s]);
         }
-        if (ok && lane == 0) {
-          mma_commit(&empty[s]);
-          mma_commit(&abar[c & 1]);
+        if (!ok) {
+          atomicOr((int*)&s_fail, 1);
+          break;
         }
-        __syncwarp();
-      }
-      if (!ok) {
-        atomicOr((int*)&s_fail, 1);
-        break;
       }
     }
+    __syncwarp();
   } else {
     // ------------------------------------------------------- A operand, drain
     const int m = tid;  // tensor-memory lane = row of A
@@ -456,7 +463,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_ttmc_tc(const TcArgs a) {
       const int s = c % kStages;
       unsigned char* st = sm + s * a.stage_bytes;
       bool ok = wait_warp(&full[s], (uint32_t)((c / kStages) & 1), a.cap, fail);
-      if (ok && c >= 2) ok = wait_warp(&abar[c & 1], (uint32_t)(((c - 2) >> 1) & 1), a.cap, fail);
+      // A buffer c & 1 is free once the MMAs of chunk c - 2 are done
+      if (ok && c >= 2) ok = wait_warp(&empty[(c - 2) % kStages], (uint32_t)(((c - 2) / kStages) & 1), a.cap, fail);
       if (!ok) {
         atomicOr((int*)&s_fail, 1);
         break;
@@ -741,8 +749,8 @@ void tk_ttmc_tc_launch(tucker_ctx* c, int n, void* const* F, const int* ldF, con
   a.Zpart = (float*)c->Zpart;
   a.err = c->err;
   a.cap = c->wait_cap;
-  // stages | barriers (2 kStages + 4 + 2 kNacc + 1) | TMEM slot (8 B) | running sums (NP x 128 floats)
-  const size_t smem = 1024 + (size_t)kStages * a.stage_bytes + (2 * kStages + 4 + 2 * kNacc + 2) * 8 +
+  // stages | barriers (2 kStages + 2 + 2 kNacc + 1) | TMEM slot (8 B) | running sums (NP x 128 floats)
+  const size_t smem = 1024 + (size_t)kStages * a.stage_bytes + (2 * kStages + 2 + 2 * kNacc + 2) * 8 +
                       (size_t)a.NP * 128 * 4;
   const int nvr = std::max(a.nv[0], std::max(a.nv[1], a.nv[2]));
   // loader registers: kU chunks' rows of kNVR vectors within the 96 registers of two CTAs per SM

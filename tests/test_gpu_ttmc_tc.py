@@ -1,5 +1,5 @@
 """GPU parity of the tensor-core TTM-chain (eq. (1) as per-slice MMAs over
-8-element blocks, 3xTF32) against the FP64 oracle, and against the CUDA-core
+8-element blocks, 3xTF32 in two MMAs) against the FP64 oracle, and against the CUDA-core
 form of the same context options: 4-mode FP32 tensors with K_a K_b in
 [32, 128], K_c <= 48 and Khat >= 256 (N = 16 and N = 32 accumulator widths)."""
 import numpy as np
@@ -105,5 +105,27 @@ def test_tensor_core_ttm_chain_sparse_and_ragged():
     Fd, Fo = factors(c["L"], K, 12, "fp32")
     for n in range(4):
         assert tk.ttm_form(n)["tensor_cores"]
+        check_ttm(tk, c, Fd, Fo, n, "fp32")
+    tk.close()
+
+
+def test_tensor_core_ttm_chain_forced_wait_cap_reports_timeout():
+    """wait_cap = -1 makes every mbarrier wait give up at once, including the
+    tensor-core TTM-chain's (its MMA issuer's single-thread waits too): a whole
+    invocation on a 4-mode context whose every mode takes the tensor cores
+    reports TUCKER_ERR_TIMEOUT at its synchronising end, and a context without
+    the cap then matches the oracle on the same GPU."""
+    from paper_1804_09494_gb300.tucker import TuckerError
+    c = case((400, 300, 60, 20), 60_000, (1.2, 1.2, None, None), "uniform", seed=25)
+    K = (10, 10, 10, 10)
+    Fd, Fo = factors(c["L"], K, 9, "fp32")
+    tk = make(c, K, "fp32", wait_cap=-1)
+    assert all(tk.ttm_form(n)["tensor_cores"] for n in range(4))
+    with pytest.raises(TuckerError) as e:
+        tk.hooi_iter([f.clone() for f in Fd], want_fit=True)
+    assert e.value.status == "ERR_TIMEOUT", str(e.value)
+    tk.close()
+    tk = make(c, K, "fp32")
+    for n in range(4):
         check_ttm(tk, c, Fd, Fo, n, "fp32")
     tk.close()
