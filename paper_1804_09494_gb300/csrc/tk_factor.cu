@@ -538,6 +538,7 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16);
   const EigSmem<T> sh_ck{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
   __shared__ int conv_flag;
+  bool conv = false;  // the Lanczos run stopped at a successful check
   if (a.clk && tid == 0) a.clk[0] = clock64();
 
   // ---- Lanczos
@@ -594,6 +595,7 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
       __syncthreads();
       if (lanczos_converged<T, 1024>(a, sh_ck, j + 1, ta, tb, tb2, a.tri, bnorm, fro, eps, &conv_flag)) {
         m = j + 1;
+        conv = true;
         break;
       }
     }
@@ -621,7 +623,8 @@ __global__ void __launch_bounds__(1024) k_eig(const EigArgs<T> a) {
   __syncthreads();
   if (a.clk && tid == 0) a.clk[1] = clock64();
 
-  eig_tridiag_topk<T, 1024>(a, sh_ck, m, ta, tb, tb2, a.tri, fro, eps);
+  // a successful early-stop check has solved this very T_m into a.tri already
+  if (!conv) eig_tridiag_topk<T, 1024>(a, sh_ck, m, ta, tb, tb2, a.tri, fro, eps);
   if (a.clk && tid == 0) a.clk[3] = clock64();
   // ---- X = Q S, then modified Gram-Schmidt (separates clustered eigenvalues)
   for (int idx = tid; idx < n * K; idx += nt) {
@@ -874,6 +877,7 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
   const T eps = sizeof(T) == 4 ? T(1.2e-7) : T(2.3e-16);
   const EigSmem<T> sh_ck{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
   __shared__ int conv_flag;
+  bool conv = false;  // the Lanczos run stopped at a successful check
   if (a.clk && tid == 0) a.clk[0] = clock64();
 
   // rows owned by this thread (n <= 2 * NT)
@@ -966,6 +970,7 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
       __syncthreads();
       if (lanczos_converged<T, 128>(a, sh_ck, j + 1, ta, tb, tb2, a.tri, bnorm, fro, eps, &conv_flag)) {
         m = j + 1;
+        conv = true;
         break;
       }
     }
@@ -994,11 +999,13 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_small(const EigArgs<T>
   if (a.clk && tid == 0) a.clk[1] = clock64();
 
   const EigSmem<T> sh{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
-  eig_tridiag_topk<T>(a, sh, m, ta, tb, tb2, tri, fro, eps);
+  // a successful early-stop check has solved this very T_m into a.tri already
+  const T* trix = conv ? a.tri : tri;
+  if (!conv) eig_tridiag_topk<T>(a, sh, m, ta, tb, tb2, tri, fro, eps);
   // ---- X = Q S (row r of X from row r of Q)
   for (int idx = tid; idx < n * K; idx += NT) {
     const int r = idx / K, k = idx - r * K;
-    const T* x = tri + (size_t)k * 6 * m + 5 * m;
+    const T* x = trix + (size_t)k * 6 * m + 5 * m;
     const T* qr = Q + (size_t)r * ldq;
     T s0 = T(0), s1 = T(0);
     int j = 0;
@@ -1076,6 +1083,7 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_v4(const EigArgs<float
   const float eps = 1.2e-7f;
   const EigSmem<float> sh_ck{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
   __shared__ int conv_flag;
+  bool conv = false;  // the Lanczos run stopped at a successful check
   if (a.clk && tid == 0) a.clk[0] = clock64();
 
   const int r = tid;
@@ -1147,6 +1155,7 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_v4(const EigArgs<float
       __syncthreads();
       if (lanczos_converged<float, 128>(a, sh_ck, j + 1, ta, tb, tb2, a.tri, bnorm, fro, eps, &conv_flag)) {
         m = j + 1;
+        conv = true;
         break;
       }
     }
@@ -1178,11 +1187,13 @@ __global__ void __launch_bounds__(kEigSmallThreads) k_eig_v4(const EigArgs<float
   if (a.clk && tid == 0) a.clk[1] = clock64();
 
   const EigSmem<float> sh{red, lo_s, hi_s, lam_s, inv_sig, cnt_s, mn_s, mx_s, b2_s};
-  eig_tridiag_topk<float>(a, sh, m, ta, tb, tb2, tri, fro, eps);
+  // a successful early-stop check has solved this very T_m into a.tri already
+  const float* trix = conv ? a.tri : tri;
+  if (!conv) eig_tridiag_topk<float>(a, sh, m, ta, tb, tb2, tri, fro, eps);
   // ---- X = Q S (row r of X from row r of Q)
   for (int idx = tid; idx < n * K; idx += NT) {
     const int rr = idx / K, k = idx - rr * K;
-    const float* x = tri + (size_t)k * 6 * m + 5 * m;
+    const float* x = trix + (size_t)k * 6 * m + 5 * m;
     const float* qr = Q + (size_t)rr * ld;
     float s0 = 0.f, s1 = 0.f;
     int j = 0;
